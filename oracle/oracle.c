@@ -1,0 +1,150 @@
+/*
+ * Plain FP64 CPU oracle for the RPA polarization chi0(q, i omega_l) in the mixed product
+ * basis, the dielectric matrix eps and the screened Coulomb interaction W.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the reference the CUDA library is checked against.
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may load it; the
+ * library never calls it, and it shares no code, header or table with the library.
+ *
+ * Everything is a direct transcription of the definitions, in double precision, with plain
+ * loops (OpenMP over independent output entries only; every sum runs in a fixed order):
+ *
+ *   Eq. (polfx), Sec. 2: Pi_{mu nu}(q, w) = sum_k sum_{n occ} sum_{n' unocc} Z_mu Z_nu^*
+ *        [ 1/(w - Delta + i delta) - 1/(w + Delta - i delta) ],  Delta = e_{q+k n'} - e_{k n}.
+ *   On the imaginary axis w = i omega_l with delta -> 0 the bracket is
+ *        1/(i omega - Delta) - 1/(i omega + Delta) = -2 Delta / (Delta^2 + omega^2).
+ *   Index convention (the conjugate sits on the row index):
+ *        chi0_IJ(l) = s * sum_r w_l(Delta_r) conj(z_{I,r}) z_{J,r},
+ *   which is the transpose (= complex conjugate) of the paper's Pi_{mu nu} for the same Z.
+ *   No 1/N_k factor: any Brillouin-zone weight is carried by Z or by the spin factor s.
+ *
+ *   Eq. (dielectricfunction): eps_{mu nu} = delta_{mu nu} - sqrt(v_mu) Pi_{mu nu} sqrt(v_nu)
+ *   Eq. (screenedcoulomb):    W_{mu nu}   = sqrt(v_mu) eps^{-1}_{mu nu} sqrt(v_nu)
+ *   Eq. (wc):                 W^c_{mu nu} = sqrt(v_mu) (eps^{-1}_{mu nu} - delta_{mu nu}) sqrt(v_nu)
+ *   eps is Hermitian positive definite (eps >= I because chi0(i omega) is negative
+ *   semidefinite, Sec. 2), so eps^{-1} is formed by a textbook Cholesky factorisation
+ *   eps = L L^H followed by forward and backward substitution against the identity.
+ *
+ * Matrices are column-major per frequency: element (i, j) of frequency l is at
+ * l*N*N + j*N + i.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+
+typedef double complex zdouble;
+
+/* Sec. 2, Eq. (polfx) at w = i omega, delta -> 0. */
+double oracle_weight(double delta, double omega) { return -2.0 * delta / (delta * delta + omega * omega); }
+
+/* Transition energies of one k-point, r = n * n_unocc + m: Delta_r = e_unocc[m] - e_occ[n].
+ * Returns the number of columns with Delta <= 0 or non-finite (the method needs Delta > 0). */
+int oracle_delta(int n_occ, int n_unocc, const double *eps_occ, const double *eps_unocc, double *delta) {
+  int bad = 0;
+  for (int n = 0; n < n_occ; ++n)
+    for (int m = 0; m < n_unocc; ++m) {
+      double d = eps_unocc[m] - eps_occ[n];
+      delta[(size_t)n * n_unocc + m] = d;
+      if (!(d > 0.0) || !isfinite(d)) ++bad;
+    }
+  return bad;
+}
+
+/* chi0 restricted to rows I in a set and columns J in a set, every frequency:
+ *   out[(l * nJ + j) * nI + i] = s * sum_{r<K} w_l(Delta_r) conj(ZI[i*K + r]) ZJ[j*K + r]
+ * ZI is (nI x K) row-major (row i holds z_{I_i, r} for all r), ZJ likewise.
+ * With ZI = ZJ = all rows this is the full matrix in the column-major layout above. */
+void oracle_chi0_rows(long long K, int nI, const zdouble *ZI, int nJ, const zdouble *ZJ, const double *delta, int L,
+                      const double *omega, double spin, zdouble *out) {
+  double *wl = (double *)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
+  for (int l = 0; l < L; ++l) {
+    for (long long r = 0; r < K; ++r) wl[r] = oracle_weight(delta[r], omega[l]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < nJ; ++j) {
+      const zdouble *zj = ZJ + (size_t)j * K;
+      for (int i = 0; i < nI; ++i) {
+        const zdouble *zi = ZI + (size_t)i * K;
+        zdouble acc = 0.0;
+        for (long long r = 0; r < K; ++r) acc += wl[r] * (conj(zi[r]) * zj[r]);
+        out[((size_t)l * nJ + j) * nI + i] = spin * acc;
+      }
+    }
+  }
+  free(wl);
+}
+
+/* Eq. (dielectricfunction): eps = I - D chi D with D = diag(sqrt(v)), one frequency. */
+void oracle_eps(int N, const zdouble *chi, const double *v, zdouble *eps) {
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < N; ++i)
+      eps[(size_t)j * N + i] = (i == j ? 1.0 : 0.0) - sqrt(v[i]) * chi[(size_t)j * N + i] * sqrt(v[j]);
+}
+
+/* Textbook Cholesky eps = L L^H on the lower triangle (column-major, L overwrites a copy).
+ * Returns 0 on success, or j+1 if the j-th pivot is not positive (eps not HPD). */
+int oracle_cholesky(int N, const zdouble *A, zdouble *Lf) {
+  for (size_t t = 0; t < (size_t)N * N; ++t) Lf[t] = 0.0;
+  for (int j = 0; j < N; ++j) {
+    double d = creal(A[(size_t)j * N + j]);
+    for (int k = 0; k < j; ++k) {
+      zdouble ljk = Lf[(size_t)k * N + j];
+      d -= creal(ljk * conj(ljk));
+    }
+    if (!(d > 0.0)) return j + 1;
+    double ljj = sqrt(d);
+    Lf[(size_t)j * N + j] = ljj;
+#pragma omp parallel for schedule(static)
+    for (int i = j + 1; i < N; ++i) {
+      zdouble s = A[(size_t)j * N + i];
+      for (int k = 0; k < j; ++k) s -= Lf[(size_t)k * N + i] * conj(Lf[(size_t)k * N + j]);
+      Lf[(size_t)j * N + i] = s / ljj;
+    }
+  }
+  return 0;
+}
+
+/* eps^{-1} from the Cholesky factor: solve L Y = I, then L^H X = Y, column by column. */
+void oracle_cholesky_inverse(int N, const zdouble *Lf, zdouble *X) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int c = 0; c < N; ++c) {
+    zdouble *x = X + (size_t)c * N;
+    for (int i = 0; i < N; ++i) {           /* forward: L y = e_c */
+      zdouble s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= Lf[(size_t)k * N + i] * x[k];
+      x[i] = s / Lf[(size_t)i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {      /* backward: L^H x = y, (L^H)_{ik} = conj(L_{ki}) */
+      zdouble s = x[i];
+      for (int k = i + 1; k < N; ++k) s -= conj(Lf[(size_t)i * N + k]) * x[k];
+      x[i] = s / conj(Lf[(size_t)i * N + i]);
+    }
+  }
+}
+
+/* eps, W = D eps^{-1} D and W^c = W - diag(v) for every frequency (Eqs. dielectricfunction,
+ * screenedcoulomb, wc). `work` holds N*N complex values. info[l] = 0 or the failed pivot+1;
+ * W and W^c of a failed frequency are left as zero. eps_out / Wc_out may be NULL. */
+void oracle_eps_w(int N, int L, const zdouble *chi, const double *v, zdouble *eps_out, zdouble *W_out, zdouble *Wc_out,
+                  int *info, zdouble *work_eps, zdouble *work_l) {
+  size_t NN = (size_t)N * N;
+  for (int l = 0; l < L; ++l) {
+    oracle_eps(N, chi + l * NN, v, work_eps);
+    if (eps_out)
+      for (size_t t = 0; t < NN; ++t) eps_out[l * NN + t] = work_eps[t];
+    zdouble *W = W_out + l * NN;
+    info[l] = oracle_cholesky(N, work_eps, work_l);
+    if (info[l] != 0) {
+      for (size_t t = 0; t < NN; ++t) W[t] = 0.0;
+      if (Wc_out)
+        for (size_t t = 0; t < NN; ++t) Wc_out[l * NN + t] = 0.0;
+      continue;
+    }
+    oracle_cholesky_inverse(N, work_l, W); /* W <- eps^{-1} */
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) W[(size_t)j * N + i] *= sqrt(v[i]) * sqrt(v[j]);
+    if (Wc_out)
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i < N; ++i) Wc_out[l * NN + (size_t)j * N + i] = W[(size_t)j * N + i] - (i == j ? v[i] : 0.0);
+  }
+}
