@@ -1,0 +1,144 @@
+/*
+ * qsgw.h — C ABI of the GB300 (sm_103a) library that assembles the RPA polarization
+ * chi0(q, i omega) in the mixed product basis and forms eps and W from it
+ * (Obata, Kotani, Oda, "Efficient implementation of the quasiparticle self-consistent GW
+ * method on GPU", arXiv:2506.03477).
+ *
+ * What is computed (Sec. 2, Eq. (polfx) on the imaginary axis, delta -> 0):
+ *
+ *   chi0_IJ(q, i omega_l) = s * sum_{k, n occ, m unocc} w_l(Delta_knm) conj(z_{I,knm}) z_{J,knm}
+ *   w_l(Delta) = 1/(i omega_l - Delta) - 1/(i omega_l + Delta) = -2 Delta / (Delta^2 + omega_l^2)
+ *   Delta_knm  = eps_unocc[k, m] - eps_occ[k, n]  (must be > 0)
+ *
+ * i.e. chi0(l) = -s * Y_l^H Y_l with Y_l = diag(sqrt|w_l|) Z^T: a Hermitian rank-K update per
+ * frequency. The conjugate sits on the row index I, so chi0 is the transpose (equivalently
+ * the complex conjugate) of the paper's Pi_{mu nu} = sum Z_mu Z_nu^* for the same Z. There is no
+ * 1/N_k factor; Brillouin-zone weights belong in Z or in s.
+ *
+ *   eps_IJ = delta_IJ - sqrt(v_I) chi0_IJ sqrt(v_J)       Eq. (dielectricfunction)
+ *   W_IJ   = sqrt(v_I) [eps^{-1}]_IJ sqrt(v_J)            Eq. (screenedcoulomb)
+ *   W^c_IJ = W_IJ - v_I delta_IJ                          Eq. (wc)
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are interleaved (re, im) pairs of double (C99 double complex layout).
+ *   - Matrices are column-major: element (I, J) of an n_pb x n_pb matrix is at J*n_pb + I.
+ *     A stack over frequencies is [n_omega][n_pb][n_pb], frequency slowest.
+ *   - Device pointers are CUDA global-memory pointers on the context's current device.
+ *     Where a call says "device or host", the library detects pageable/pinned host memory
+ *     with cudaPointerGetAttributes and stages it through device memory it owns.
+ *   - The caller owns all inputs and outputs; the library only borrows them until the stream
+ *     work of the call has completed. The context owns its accumulators and scratch.
+ *   - Every call is asynchronous and ordered on the stream given to qsgw_chi0_init, except
+ *     where stated. Argument errors are returned synchronously and leave the context
+ *     unchanged. Errors found on the device (Delta <= 0, a bounded wait that gave up) are
+ *     sticky: they are returned by the next qsgw_chi0_finalize, qsgw_eps_inv, qsgw_chi0_sync
+ *     or qsgw_chi0_destroy, which synchronise the stream.
+ *   - Not thread-safe: one host thread per context at a time.
+ */
+#ifndef QSGW_H
+#define QSGW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsgw_ctx qsgw_ctx; /* opaque; created by qsgw_chi0_init, owned by the library */
+
+typedef enum {
+  QSGW_OK = 0,
+  QSGW_ERR_ARG = -1,     /* invalid argument (returned synchronously) */
+  QSGW_ERR_DOMAIN = -2,  /* some Delta <= 0 or non-finite (device-detected, sticky) */
+  QSGW_ERR_NOMEM = -3,   /* device allocation failed */
+  QSGW_ERR_CUDA = -4,    /* a CUDA runtime / library call failed */
+  QSGW_ERR_NOT_PD = -5,  /* eps not positive definite at some frequency (see info) */
+  QSGW_ERR_TIMEOUT = -6, /* a bounded device-side wait gave up (sticky) */
+  QSGW_ERR_STATE = -7    /* call not valid in the context's current state */
+} qsgw_status;
+
+typedef enum {
+  QSGW_FP64 = 0,        /* FP64 arithmetic end to end (CUDA-core DFMA) */
+  QSGW_MIXED_BF16X3 = 1 /* tcgen05 tensor cores on exact 3-digit BF16 slices, FP32 per chunk,
+                           double-float (2 x FP32) across chunks; eps and W stay FP64 */
+} qsgw_prec;
+
+/* Create a context for n_q independent q-points (Alg. 1 loops over q; each q has its own
+ * n_pb[q] product-basis size and its own accumulator).
+ *   ctx          out: new context (NULL on error)
+ *   n_q          number of q-points, >= 1
+ *   n_pb         host [n_q], each in [1, 16384]
+ *   n_omega      number of imaginary frequencies, in [1, 16]
+ *   omega        host [n_omega], omega_l in Ry, finite and >= 0 (sign is irrelevant: Pi(w) = Pi(-w))
+ *   spin_factor  s in the formula above (2 for a spin-degenerate system), finite
+ *   prec         arithmetic of the chi0 assembly
+ *   cuda_stream  cudaStream_t all work is ordered on (NULL = legacy default stream)
+ * Allocates the accumulators (zeroed); returns QSGW_ERR_NOMEM if they do not fit. */
+qsgw_status qsgw_chi0_init(qsgw_ctx **ctx, int n_q, const int *n_pb, int n_omega, const double *omega,
+                           double spin_factor, qsgw_prec prec, void *cuda_stream);
+
+/* Add one block of transition columns, normally one k-point, to chi0(q) (the k / n / n'
+ * sums of Eq. (polfx); Alg. 1 accumulates Im Pi per k-point and batch of n').
+ *   Z          device or host, complex128, column-major n_pb[q] x (n_occ*n_unocc) with leading
+ *              dimension ldz >= n_pb[q]; column r = n*n_unocc + m holds z_{I, k n m}
+ *              (unoccupied index fastest, as the paper's Z(1:n_pb, n', n))
+ *   eps_occ    device or host [n_occ], eps_unocc device or host [n_unocc], Ry
+ *   n_omega, omega  must equal the grid given to qsgw_chi0_init (host), else QSGW_ERR_ARG
+ * Columns with Delta <= 0 or non-finite contribute nothing and set QSGW_ERR_DOMAIN (sticky).
+ * The result does not depend on how columns are split across calls, up to rounding. */
+qsgw_status qsgw_chi0_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_unocc,
+                                 const double *eps_occ, const double *eps_unocc, int n_omega, const double *omega);
+
+/* Write chi0(q) (the scaled, mirrored accumulator: full Hermitian, imaginary part of the
+ * diagonal exactly zero) into chi0, device complex128 [n_omega][n_pb][n_pb]. Synchronises
+ * the stream and returns any sticky device error. The accumulator is kept. */
+qsgw_status qsgw_chi0_finalize(qsgw_ctx *ctx, int q, void *chi0);
+
+/* From the current accumulator of q: eps (Eq. dielectricfunction), its FP64 Cholesky
+ * factorisation and inverse, and W (Eq. screenedcoulomb), or W^c (Eq. wc) when
+ * correlation_only != 0, for every frequency.
+ *   v         device [n_pb], Coulomb eigenvalues v_I > 0 (diagonal MPB basis, Eq. (eqvcoue))
+ *   W         device complex128 [n_omega][n_pb][n_pb], full Hermitian
+ *   eps_out   NULL or device complex128, same layout: eps before factorisation
+ *   info      host [n_omega]: 0, or j+1 if the j-th Cholesky pivot was not positive; the W of
+ *             such a frequency is left unspecified and QSGW_ERR_NOT_PD is returned
+ * Synchronises the stream. */
+qsgw_status qsgw_eps_inv(qsgw_ctx *ctx, int q, const double *v, void *W, void *eps_out, int correlation_only,
+                         int *info);
+
+/* Zero the accumulator of q (start a new chi0(q)). Asynchronous. */
+qsgw_status qsgw_chi0_reset(qsgw_ctx *ctx, int q);
+
+/* Wait for all queued work; return and clear any sticky device error. */
+qsgw_status qsgw_chi0_sync(qsgw_ctx *ctx);
+
+/* Free everything the context owns. Synchronises first; returns any sticky device error. */
+qsgw_status qsgw_chi0_destroy(qsgw_ctx *ctx);
+
+/* Static, human-readable name of a status code. */
+const char *qsgw_status_string(qsgw_status s);
+
+/* ---- synthetic inputs (not part of the paper's method) --------------------------------
+ * The paper's Z comes from PMT eigenfunctions (Eq. (defz)), which are not available. These
+ * entry points draw Z on the device from Philox4x32-10 with the same counter layout as the
+ * host-side generator used by the tests:
+ *   key = (seed, (gen_q << 8) | 0), counter = (k, n, m, I);
+ *   u1 = ((w0 << 21 | w1 >> 11) + 1) * 2^-53, u2 = (w2 << 21 | w3 >> 11) * 2^-53;
+ *   z = sqrt(-ln u1) (cos 2 pi u2 + i sin 2 pi u2) / (1 + I / s_div). */
+
+/* Fill Z (device complex128, column-major n_pb x (n_occ*n_unocc), leading dimension ldz)
+ * with the synthetic Z of k-point k. Asynchronous on `cuda_stream`. */
+qsgw_status qsgw_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, int n_occ, int n_unocc, double s_div,
+                         void *Z, long long ldz, void *cuda_stream);
+
+/* Accumulate k-points k_begin..k_end-1 of the synthetic Z into chi0(q) without ever storing
+ * the whole Z: each k-point is drawn into context-owned device scratch, then accumulated.
+ *   eps_occ    device [k_end-k_begin][n_occ]
+ *   eps_unocc  device, the per-k blocks concatenated; block i has n_unocc_per_k[i] entries
+ *   n_unocc_per_k  host [k_end-k_begin] */
+qsgw_status qsgw_chi0_accumulate_synthetic(qsgw_ctx *ctx, int q, unsigned long long seed, int gen_q, int k_begin,
+                                           int k_end, int n_occ, const int *n_unocc_per_k, const double *eps_occ,
+                                           const double *eps_unocc, double s_div);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSGW_H */

@@ -1,0 +1,341 @@
+// C ABI (include/qsgw.h): context, argument validation, host staging, stream ordering, and
+// the eps^{-1} step through cuSOLVER (FP64 Cholesky: potrf + potri).
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+#include "mixed.cuh"
+
+using namespace qsgw;
+
+struct QAcc {
+  int n_pb = 0;
+  int n_pad = 0;
+  void* acc = nullptr;  // FP64: double2 [L][n_pad][n_pad]; mixed: float4 (double-float complex), same indexing
+  size_t bytes = 0;
+};
+
+struct qsgw_ctx {
+  int device = 0;
+  int n_q = 0;
+  OmegaGrid g{};
+  double omega[kMaxOmega] = {};
+  double spin = 2.0;
+  qsgw_prec prec = QSGW_FP64;
+  cudaStream_t stream = nullptr;
+  std::vector<QAcc> q;
+  int* d_err = nullptr;
+  // scratch, grown on demand
+  double* d_w = nullptr;
+  size_t w_cap = 0;  // doubles
+  void* d_zstage = nullptr;
+  size_t zstage_cap = 0;  // bytes
+  double* d_estage = nullptr;
+  size_t estage_cap = 0;  // doubles
+  MixedScratch mixed;
+  cusolverDnHandle_t solver = nullptr;
+  void* solver_ws = nullptr;
+  size_t solver_ws_bytes = 0;
+  int* d_info = nullptr;
+};
+
+namespace {
+
+qsgw_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QSGW_OK;
+  if (e == cudaErrorMemoryAllocation) return QSGW_ERR_NOMEM;
+  return QSGW_ERR_CUDA;
+}
+
+#define QSGW_CK(expr)                                   \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) return cuda_status(e_);      \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+qsgw_status grow(void** p, size_t* cap, size_t need_bytes) {
+  if (*cap >= need_bytes) return QSGW_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  QSGW_CK(cudaMalloc(p, need_bytes));
+  *cap = need_bytes;
+  return QSGW_OK;
+}
+
+// Read and clear the sticky device error (synchronises the stream).
+qsgw_status take_device_error(qsgw_ctx* c) {
+  QSGW_CK(cudaStreamSynchronize(c->stream));
+  int h = 0;
+  QSGW_CK(cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != DEV_OK) {
+    QSGW_CK(cudaMemset(c->d_err, 0, sizeof(int)));
+    return h == DEV_DOMAIN ? QSGW_ERR_DOMAIN : QSGW_ERR_TIMEOUT;
+  }
+  return QSGW_OK;
+}
+
+qsgw_status check_grid(const qsgw_ctx* c, int n_omega, const double* omega) {
+  if (n_omega != c->g.L || !omega) return QSGW_ERR_ARG;
+  for (int l = 0; l < n_omega; ++l)
+    if (std::memcmp(&omega[l], &c->omega[l], sizeof(double)) != 0) return QSGW_ERR_ARG;
+  return QSGW_OK;
+}
+
+// Core of accumulate once every pointer is on the device.
+qsgw_status accumulate_device(qsgw_ctx* c, int q, const double2* Z, long long ldz, int n_occ, int n_unocc,
+                              const double* eo, const double* eu) {
+  QAcc& a = c->q[q];
+  const long long K = (long long)n_occ * n_unocc;
+  if (c->prec == QSGW_FP64) {
+    qsgw_status st = grow(reinterpret_cast<void**>(&c->d_w), &c->w_cap, sizeof(double) * (size_t)K * c->g.L);
+    if (st != QSGW_OK) return st;
+    launch_weights_fp64(eo, eu, n_occ, n_unocc, c->g, c->d_w, K, c->d_err, c->stream);
+    launch_herk_fp64(Z, ldz, a.n_pb, a.n_pad, K, c->d_w, K, c->g.L, static_cast<double2*>(a.acc), c->stream);
+  } else {
+    qsgw_status st = mixed_accumulate(c->mixed, Z, ldz, a.n_pb, a.n_pad, n_occ, n_unocc, eo, eu, c->g,
+                                      static_cast<float4*>(a.acc), c->d_err, c->stream);
+    if (st != QSGW_OK) return st;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qsgw_status_string(qsgw_status s) {
+  switch (s) {
+    case QSGW_OK: return "QSGW_OK";
+    case QSGW_ERR_ARG: return "QSGW_ERR_ARG: invalid argument";
+    case QSGW_ERR_DOMAIN: return "QSGW_ERR_DOMAIN: a transition energy Delta <= 0 or non-finite";
+    case QSGW_ERR_NOMEM: return "QSGW_ERR_NOMEM: device allocation failed";
+    case QSGW_ERR_CUDA: return "QSGW_ERR_CUDA: CUDA runtime or library error";
+    case QSGW_ERR_NOT_PD: return "QSGW_ERR_NOT_PD: eps not positive definite at some frequency";
+    case QSGW_ERR_TIMEOUT: return "QSGW_ERR_TIMEOUT: a bounded device wait gave up";
+    case QSGW_ERR_STATE: return "QSGW_ERR_STATE: call not valid in this state";
+  }
+  return "QSGW: unknown status";
+}
+
+qsgw_status qsgw_chi0_init(qsgw_ctx** out, int n_q, const int* n_pb, int n_omega, const double* omega,
+                           double spin_factor, qsgw_prec prec, void* cuda_stream) {
+  if (!out) return QSGW_ERR_ARG;
+  *out = nullptr;
+  if (n_q < 1 || !n_pb || n_omega < 1 || n_omega > kMaxOmega || !omega || !std::isfinite(spin_factor))
+    return QSGW_ERR_ARG;
+  if (prec != QSGW_FP64 && prec != QSGW_MIXED_BF16X3) return QSGW_ERR_ARG;
+  for (int i = 0; i < n_q; ++i)
+    if (n_pb[i] < 1 || n_pb[i] > kMaxNpb) return QSGW_ERR_ARG;
+  for (int l = 0; l < n_omega; ++l)
+    if (!std::isfinite(omega[l]) || omega[l] < 0.0) return QSGW_ERR_ARG;
+
+  qsgw_ctx* c = new (std::nothrow) qsgw_ctx();
+  if (!c) return QSGW_ERR_NOMEM;
+  c->n_q = n_q;
+  c->spin = spin_factor;
+  c->prec = prec;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->g.L = n_omega;
+  for (int l = 0; l < n_omega; ++l) {
+    c->omega[l] = omega[l];
+    c->g.w2[l] = omega[l] * omega[l];
+    c->g.w2f[l] = (float)(omega[l] * omega[l]);
+  }
+  qsgw_status st = QSGW_OK;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) st = cuda_status(e);
+  c->q.resize(n_q);
+  for (int i = 0; i < n_q && st == QSGW_OK; ++i) {
+    QAcc& a = c->q[i];
+    a.n_pb = n_pb[i];
+    a.n_pad = pad_to(n_pb[i], kPad);
+    a.bytes = (size_t)a.n_pad * a.n_pad * n_omega * (prec == QSGW_FP64 ? sizeof(double2) : sizeof(float4));
+    e = cudaMalloc(&a.acc, a.bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.acc, 0, a.bytes, c->stream);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  if (st == QSGW_OK) st = cuda_status(cudaStreamSynchronize(c->stream));
+  if (st != QSGW_OK) {
+    qsgw_chi0_destroy(c);
+    return st;
+  }
+  *out = c;
+  return QSGW_OK;
+}
+
+qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
+                                 const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
+  if (!c || q < 0 || q >= c->n_q || !Z || !eps_occ || !eps_unocc) return QSGW_ERR_ARG;
+  const QAcc& a = c->q[q];
+  if (ldz < a.n_pb || n_occ < 1 || n_unocc < 1) return QSGW_ERR_ARG;
+  if ((long long)n_occ * n_unocc > (1LL << 31)) return QSGW_ERR_ARG;
+  qsgw_status st = check_grid(c, n_omega, omega);
+  if (st != QSGW_OK) return st;
+  const long long K = (long long)n_occ * n_unocc;
+
+  const double* eo = eps_occ;
+  const double* eu = eps_unocc;
+  if (!is_device_ptr(eps_occ) || !is_device_ptr(eps_unocc)) {
+    st = grow(reinterpret_cast<void**>(&c->d_estage), &c->estage_cap, sizeof(double) * (size_t)(n_occ + n_unocc));
+    if (st != QSGW_OK) return st;
+    QSGW_CK(cudaMemcpyAsync(c->d_estage, eps_occ, sizeof(double) * n_occ, cudaMemcpyDefault, c->stream));
+    QSGW_CK(cudaMemcpyAsync(c->d_estage + n_occ, eps_unocc, sizeof(double) * n_unocc, cudaMemcpyDefault, c->stream));
+    eo = c->d_estage;
+    eu = c->d_estage + n_occ;
+  }
+  const double2* Zd = static_cast<const double2*>(Z);
+  if (!is_device_ptr(Z)) {
+    const size_t bytes = sizeof(double2) * (size_t)ldz * (size_t)K;
+    st = grow(&c->d_zstage, &c->zstage_cap, bytes);
+    if (st != QSGW_OK) return st;
+    QSGW_CK(cudaMemcpyAsync(c->d_zstage, Z, bytes, cudaMemcpyDefault, c->stream));
+    Zd = static_cast<const double2*>(c->d_zstage);
+  }
+  return accumulate_device(c, q, Zd, ldz, n_occ, n_unocc, eo, eu);
+}
+
+qsgw_status qsgw_chi0_finalize(qsgw_ctx* c, int q, void* chi0) {
+  if (!c || q < 0 || q >= c->n_q || !chi0) return QSGW_ERR_ARG;
+  const QAcc& a = c->q[q];
+  launch_finalize_chi(a.acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, a.n_pb, a.n_pad, c->g.L, c->spin,
+                      static_cast<double2*>(chi0), c->stream);
+  QSGW_CK(cudaGetLastError());
+  return take_device_error(c);
+}
+
+qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps_out, int correlation_only,
+                         int* info) {
+  if (!c || q < 0 || q >= c->n_q || !v || !W || !info) return QSGW_ERR_ARG;
+  const QAcc& a = c->q[q];
+  const int n = a.n_pb, L = c->g.L;
+  const size_t nn = (size_t)n * n;
+  double2* w = static_cast<double2*>(W);
+  if (!c->solver) {
+    if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
+  }
+  if (cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
+  if (!c->d_info) QSGW_CK(cudaMalloc(&c->d_info, sizeof(int) * 2 * kMaxOmega));
+  int lw1 = 0, lw2 = 0;
+  if (cusolverDnZpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, n, reinterpret_cast<cuDoubleComplex*>(w), n,
+                                  &lw1) != CUSOLVER_STATUS_SUCCESS)
+    return QSGW_ERR_CUDA;
+  if (cusolverDnZpotri_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, n, reinterpret_cast<cuDoubleComplex*>(w), n,
+                                  &lw2) != CUSOLVER_STATUS_SUCCESS)
+    return QSGW_ERR_CUDA;
+  const size_t lwork = (size_t)(lw1 > lw2 ? lw1 : lw2);
+  qsgw_status st = grow(&c->solver_ws, &c->solver_ws_bytes, sizeof(cuDoubleComplex) * (lwork + 1));
+  if (st != QSGW_OK) return st;
+
+  launch_form_eps(a.acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, n, a.n_pad, L, c->spin, v, w, c->stream);
+  QSGW_CK(cudaGetLastError());
+  if (eps_out) QSGW_CK(cudaMemcpyAsync(eps_out, w, sizeof(double2) * nn * L, cudaMemcpyDeviceToDevice, c->stream));
+  auto* ws = static_cast<cuDoubleComplex*>(c->solver_ws);
+  for (int l = 0; l < L; ++l) {
+    auto* m = reinterpret_cast<cuDoubleComplex*>(w + l * nn);
+    if (cusolverDnZpotrf(c->solver, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, (int)lwork, c->d_info + l) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return QSGW_ERR_CUDA;
+    if (cusolverDnZpotri(c->solver, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, (int)lwork, c->d_info + kMaxOmega + l) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return QSGW_ERR_CUDA;
+  }
+  launch_w_from_inverse(w, n, L, v, correlation_only, c->stream);
+  QSGW_CK(cudaGetLastError());
+  int hinfo[2 * kMaxOmega];
+  QSGW_CK(cudaMemcpyAsync(hinfo, c->d_info, sizeof(int) * 2 * kMaxOmega, cudaMemcpyDeviceToHost, c->stream));
+  st = take_device_error(c);
+  if (st != QSGW_OK) return st;
+  qsgw_status res = QSGW_OK;
+  for (int l = 0; l < L; ++l) {
+    // potrf reports the first non-positive pivot (1-based); potri can only fail after a zero pivot
+    info[l] = hinfo[l] != 0 ? hinfo[l] : hinfo[kMaxOmega + l];
+    if (info[l] != 0) res = QSGW_ERR_NOT_PD;
+  }
+  return res;
+}
+
+qsgw_status qsgw_chi0_reset(qsgw_ctx* c, int q) {
+  if (!c || q < 0 || q >= c->n_q) return QSGW_ERR_ARG;
+  QSGW_CK(cudaMemsetAsync(c->q[q].acc, 0, c->q[q].bytes, c->stream));
+  return QSGW_OK;
+}
+
+qsgw_status qsgw_chi0_sync(qsgw_ctx* c) {
+  if (!c) return QSGW_ERR_ARG;
+  return take_device_error(c);
+}
+
+qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
+  if (!c) return QSGW_ERR_ARG;
+  qsgw_status st = QSGW_OK;
+  if (c->d_err) st = take_device_error(c);
+  for (auto& a : c->q)
+    if (a.acc) cudaFree(a.acc);
+  if (c->d_w) cudaFree(c->d_w);
+  if (c->d_zstage) cudaFree(c->d_zstage);
+  if (c->d_estage) cudaFree(c->d_estage);
+  mixed_free(c->mixed);
+  if (c->solver_ws) cudaFree(c->solver_ws);
+  if (c->d_info) cudaFree(c->d_info);
+  if (c->solver) cusolverDnDestroy(c->solver);
+  if (c->d_err) cudaFree(c->d_err);
+  delete c;
+  return st;
+}
+
+qsgw_status qsgw_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, int n_occ, int n_unocc, double s_div,
+                         void* Z, long long ldz, void* cuda_stream) {
+  if (!Z || n_pb < 1 || n_occ < 1 || n_unocc < 1 || ldz < n_pb || k < 0 || gen_q < 0 || gen_q > 0xFFFFFF ||
+      !(s_div > 0.0))
+    return QSGW_ERR_ARG;
+  if (!is_device_ptr(Z)) return QSGW_ERR_ARG;
+  launch_synth_z(seed, gen_q, k, n_pb, n_occ, n_unocc, s_div, static_cast<double2*>(Z), ldz,
+                 static_cast<cudaStream_t>(cuda_stream));
+  return cuda_status(cudaGetLastError());
+}
+
+qsgw_status qsgw_chi0_accumulate_synthetic(qsgw_ctx* c, int q, unsigned long long seed, int gen_q, int k_begin,
+                                           int k_end, int n_occ, const int* n_unocc_per_k, const double* eps_occ,
+                                           const double* eps_unocc, double s_div) {
+  if (!c || q < 0 || q >= c->n_q || k_begin < 0 || k_end <= k_begin || n_occ < 1 || !n_unocc_per_k || !eps_occ ||
+      !eps_unocc || !(s_div > 0.0) || gen_q < 0 || gen_q > 0xFFFFFF)
+    return QSGW_ERR_ARG;
+  if (!is_device_ptr(eps_occ) || !is_device_ptr(eps_unocc)) return QSGW_ERR_ARG;
+  const QAcc& a = c->q[q];
+  size_t max_cols = 0;
+  for (int i = 0; i < k_end - k_begin; ++i) {
+    if (n_unocc_per_k[i] < 1) return QSGW_ERR_ARG;
+    const size_t cols = (size_t)n_occ * n_unocc_per_k[i];
+    if (cols > max_cols) max_cols = cols;
+  }
+  qsgw_status st = grow(&c->d_zstage, &c->zstage_cap, sizeof(double2) * (size_t)a.n_pb * max_cols);
+  if (st != QSGW_OK) return st;
+  size_t eu_off = 0;
+  for (int i = 0; i < k_end - k_begin; ++i) {
+    const int nu = n_unocc_per_k[i];
+    auto* Zs = static_cast<double2*>(c->d_zstage);
+    launch_synth_z(seed, gen_q, k_begin + i, a.n_pb, n_occ, nu, s_div, Zs, a.n_pb, c->stream);
+    st = accumulate_device(c, q, Zs, a.n_pb, n_occ, nu, eps_occ + (size_t)i * n_occ, eps_unocc + eu_off);
+    if (st != QSGW_OK) return st;
+    eu_off += nu;
+  }
+  return QSGW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/qsgw.h"
+
+namespace qsgw {
+
+constexpr int kMaxOmega = 16;
+constexpr int kMaxNpb = 16384;
+constexpr int kPad = 64;  // accumulators are padded to a multiple of 64 rows / columns
+
+// Sticky device-side error codes (stored in ctx->d_err, first error wins).
+enum DevErr : int { DEV_OK = 0, DEV_DOMAIN = 1, DEV_TIMEOUT = 2 };
+
+struct OmegaGrid {
+  int L;
+  double w2[kMaxOmega];  // omega_l^2 (FP64)
+  float w2f[kMaxOmega];  // omega_l^2 (FP32, mixed path)
+};
+
+inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
+
+// ---- FP64 path (kernels_fp64.cu)
+// |w_l(Delta_r)| for one k-point into w[l*ldw + r] (FP64); flags Delta <= 0 / non-finite.
+void launch_weights_fp64(const double* eps_occ, const double* eps_unocc, int n_occ, int n_unocc, const OmegaGrid& g,
+                         double* w, long long ldw, int* d_err, cudaStream_t s);
+// acc[l][J][I] += sum_r w[l][r] conj(Z[I,r]) Z[J,r] on upper-triangle 64x64 tiles.
+void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
+                      long long ldw, int L, double2* acc, cudaStream_t s);
+
+// ---- shared epilogues (kernels_epsw.cu)
+// Accumulator formats: FP64 complex (double2) or double-float complex (float4 = re_hi, re_lo, im_hi, im_lo).
+enum AccKind { ACC_FP64 = 0, ACC_DF32 = 1 };
+// chi0 = -s * mirror(acc): full Hermitian, diag imag = 0 (out is [L][n][n]).
+void launch_finalize_chi(const void* acc, AccKind kind, int n, int n_pad, int L, double spin, double2* out,
+                         cudaStream_t s);
+// eps = I - D chi0 D with chi0 = -s * mirror(acc), full matrix.
+void launch_form_eps(const void* acc, AccKind kind, int n, int n_pad, int L, double spin, const double* v,
+                     double2* eps, cudaStream_t s);
+// In place: lower triangle of eps^{-1} -> full W = D eps^{-1} D (minus diag(v) if wc).
+void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, cudaStream_t s);
+
+// ---- synthetic Z (synth.cu)
+void launch_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, int n_occ, int n_unocc, double s_div,
+                    double2* Z, long long ldz, cudaStream_t s);
+
+}  // namespace qsgw

@@ -1,0 +1,117 @@
+// FP64 path: transition weights (step a1) and the FP64 complex HERK (step a4, plain form).
+//
+// chi0(l) = -s * sum_r |w_l(Delta_r)| conj(z_{I,r}) z_{J,r} with |w_l(Delta)| = 2 Delta/(Delta^2 + omega_l^2)
+// (Sec. 2, Eq. (polfx) at w = i omega). The accumulator holds the positive-weight sum; the
+// factor -s is applied when chi0 is read out.
+//
+// GB300 executes FP64 on CUDA cores at ~1 TFLOP/s (measured), so this kernel is DFMA-bound by
+// a wide margin: operands are staged through shared memory once per 16-column K-step, each
+// thread keeps a 4x4 block of complex accumulators in registers, and only tiles on or above
+// the diagonal are computed.
+#include "internal.cuh"
+
+namespace qsgw {
+
+__global__ void weights_fp64_kernel(const double* __restrict__ eo, const double* __restrict__ eu, int n_occ,
+                                    int n_unocc, OmegaGrid g, double* __restrict__ w, long long ldw, int* d_err) {
+  const long long K = (long long)n_occ * n_unocc;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < K; r += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(r / n_unocc), m = (int)(r % n_unocc);
+    const double d = eu[m] - eo[n];  // Delta_knm
+    const bool ok = (d > 0.0) && isfinite(d);
+    if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
+    for (int l = 0; l < g.L; ++l) w[l * ldw + r] = ok ? 2.0 * d / (d * d + g.w2[l]) : 0.0;
+  }
+}
+
+void launch_weights_fp64(const double* eps_occ, const double* eps_unocc, int n_occ, int n_unocc, const OmegaGrid& g,
+                         double* w, long long ldw, int* d_err, cudaStream_t s) {
+  const long long K = (long long)n_occ * n_unocc;
+  int blocks = (int)((K + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  weights_fp64_kernel<<<blocks, 256, 0, s>>>(eps_occ, eps_unocc, n_occ, n_unocc, g, w, ldw, d_err);
+}
+
+constexpr int kT = 64;   // output tile (I and J)
+constexpr int kKS = 16;  // K-step (columns staged per iteration)
+
+// grid: x = J tile, y = I tile, z = frequency. Tiles strictly below the diagonal exit at once.
+__global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
+                                                        int n_pad, long long K, const double* __restrict__ w,
+                                                        long long ldw, double2* __restrict__ acc) {
+  const int tj = blockIdx.x, ti = blockIdx.y, l = blockIdx.z;
+  if (tj < ti) return;
+  __shared__ double2 sA[kKS][kT];
+  __shared__ double2 sB[kKS][kT];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = ti * kT, j0 = tj * kT;
+  const double* wl = w + (long long)l * ldw;
+
+  double cr[4][4], ci[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) cr[a][b] = ci[a][b] = 0.0;
+
+  for (long long r0 = 0; r0 < K; r0 += kKS) {
+    __syncthreads();
+#pragma unroll
+    for (int e = tid; e < kKS * kT; e += 256) {
+      const int rr = e / kT, ii = e % kT;
+      const long long r = r0 + rr;
+      double2 za = make_double2(0.0, 0.0), zb = make_double2(0.0, 0.0);
+      if (r < K) {
+        if (i0 + ii < n_pb) za = Z[(i0 + ii) + r * ldz];
+        if (j0 + ii < n_pb) {
+          const double wr = wl[r];
+          zb = Z[(j0 + ii) + r * ldz];
+          zb.x *= wr;
+          zb.y *= wr;
+        }
+      }
+      sA[rr][ii] = za;
+      sB[rr][ii] = zb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < kKS; ++rr) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = sA[rr][ty + 16 * q];
+        b[q] = sB[rr][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          // conj(a) * b
+          cr[p][q] = fma(a[p].x, b[q].x, cr[p][q]);
+          cr[p][q] = fma(a[p].y, b[q].y, cr[p][q]);
+          ci[p][q] = fma(a[p].x, b[q].y, ci[p][q]);
+          ci[p][q] = fma(-a[p].y, b[q].x, ci[p][q]);
+        }
+    }
+  }
+  double2* out = acc + (size_t)l * n_pad * n_pad;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int I = i0 + ty + 16 * p, J = j0 + tx + 16 * q;
+      double2* o = out + (size_t)J * n_pad + I;
+      double2 v = *o;
+      v.x += cr[p][q];
+      v.y += ci[p][q];
+      *o = v;
+    }
+}
+
+void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
+                      long long ldw, int L, double2* acc, cudaStream_t s) {
+  dim3 grid(n_pad / kT, n_pad / kT, L);
+  herk_fp64_kernel<<<grid, 256, 0, s>>>(Z, ldz, n_pb, n_pad, K, w, ldw, acc);
+}
+
+}  // namespace qsgw

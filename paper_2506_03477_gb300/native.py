@@ -1,0 +1,159 @@
+"""ctypes binding for libqsgw.so (include/qsgw.h). Argument marshalling only: every step of
+the computation runs in the library's CUDA kernels (or cuSOLVER for the FP64 Cholesky).
+
+Functions keep the C names. Array arguments may be torch tensors (device or host), numpy
+arrays (host) or raw integer addresses. Any status other than QSGW_OK raises QsgwError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqsgw.so")
+
+QSGW_OK = 0
+QSGW_ERR_ARG = -1
+QSGW_ERR_DOMAIN = -2
+QSGW_ERR_NOMEM = -3
+QSGW_ERR_CUDA = -4
+QSGW_ERR_NOT_PD = -5
+QSGW_ERR_TIMEOUT = -6
+QSGW_ERR_STATE = -7
+QSGW_FP64 = 0
+QSGW_MIXED_BF16X3 = 1
+
+EXPORTS = [
+    "qsgw_chi0_init", "qsgw_chi0_accumulate", "qsgw_chi0_finalize", "qsgw_eps_inv", "qsgw_chi0_reset",
+    "qsgw_chi0_sync", "qsgw_chi0_destroy", "qsgw_status_string", "qsgw_synth_z", "qsgw_chi0_accumulate_synthetic",
+]
+
+
+class QsgwError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {qsgw_status_string(status)} ({status})")
+
+
+_lib = None
+_i, _ll, _d, _p, _u64 = ctypes.c_int, ctypes.c_longlong, ctypes.c_double, ctypes.c_void_p, ctypes.c_ulonglong
+
+
+def load():
+    """Load libqsgw.so; raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "qsgw_chi0_init": [P(_p), _i, P(_i), _i, P(_d), _d, _i, _p],
+        "qsgw_chi0_accumulate": [_p, _i, _p, _ll, _i, _i, _p, _p, _i, P(_d)],
+        "qsgw_chi0_finalize": [_p, _i, _p],
+        "qsgw_eps_inv": [_p, _i, _p, _p, _p, _i, P(_i)],
+        "qsgw_chi0_reset": [_p, _i],
+        "qsgw_chi0_sync": [_p],
+        "qsgw_chi0_destroy": [_p],
+        "qsgw_synth_z": [_u64, _i, _i, _i, _i, _i, _d, _p, _ll, _p],
+        "qsgw_chi0_accumulate_synthetic": [_p, _i, _u64, _i, _i, _i, _i, P(_i), _p, _p, _d],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = _i
+    lib.qsgw_status_string.argtypes = [_i]
+    lib.qsgw_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _check(status: int, where: str):
+    if status != QSGW_OK:
+        raise QsgwError(status, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def qsgw_status_string(status: int) -> str:
+    return load().qsgw_status_string(int(status)).decode()
+
+
+def qsgw_chi0_init(n_pb, omega, spin_factor: float, prec: int = QSGW_FP64, stream=None) -> int:
+    n_pb = list(n_pb)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    ctx = _p()
+    arr_n = (_i * len(n_pb))(*n_pb)
+    arr_o = (_d * om.size)(*om.tolist())
+    _check(load().qsgw_chi0_init(ctypes.byref(ctx), len(n_pb), arr_n, om.size, arr_o, float(spin_factor), int(prec),
+                                 _stream(stream)), "qsgw_chi0_init")
+    return ctx.value
+
+
+def qsgw_chi0_accumulate(ctx: int, q: int, Z, ldz: int, n_occ: int, n_unocc: int, eps_occ, eps_unocc, omega):
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    arr_o = (_d * om.size)(*om.tolist())
+    _check(load().qsgw_chi0_accumulate(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eps_occ),
+                                       _addr(eps_unocc), om.size, arr_o), "qsgw_chi0_accumulate")
+
+
+def qsgw_chi0_finalize(ctx: int, q: int, chi0):
+    _check(load().qsgw_chi0_finalize(ctx, q, _addr(chi0)), "qsgw_chi0_finalize")
+
+
+def qsgw_eps_inv(ctx: int, q: int, v, W, eps_out=None, correlation_only: bool = False, n_omega: int = 16,
+                 raise_not_pd: bool = True) -> np.ndarray:
+    info = (_i * 16)()
+    st = load().qsgw_eps_inv(ctx, q, _addr(v), _addr(W), _addr(eps_out), int(bool(correlation_only)), info)
+    out = np.array(info[:n_omega], dtype=np.int32)
+    if st == QSGW_ERR_NOT_PD and not raise_not_pd:
+        return out
+    _check(st, "qsgw_eps_inv")
+    return out
+
+
+def qsgw_chi0_reset(ctx: int, q: int):
+    _check(load().qsgw_chi0_reset(ctx, q), "qsgw_chi0_reset")
+
+
+def qsgw_chi0_sync(ctx: int):
+    _check(load().qsgw_chi0_sync(ctx), "qsgw_chi0_sync")
+
+
+def qsgw_chi0_destroy(ctx: int):
+    _check(load().qsgw_chi0_destroy(ctx), "qsgw_chi0_destroy")
+
+
+def qsgw_synth_z(seed: int, gen_q: int, k: int, n_pb: int, n_occ: int, n_unocc: int, s_div: float, Z, ldz: int,
+                 stream=None):
+    _check(load().qsgw_synth_z(int(seed), int(gen_q), int(k), int(n_pb), int(n_occ), int(n_unocc), float(s_div),
+                               _addr(Z), int(ldz), _stream(stream)), "qsgw_synth_z")
+
+
+def qsgw_chi0_accumulate_synthetic(ctx: int, q: int, seed: int, gen_q: int, k_begin: int, k_end: int, n_occ: int,
+                                   n_unocc_per_k, eps_occ, eps_unocc, s_div: float):
+    nu = list(n_unocc_per_k)
+    arr = (_i * len(nu))(*nu)
+    _check(load().qsgw_chi0_accumulate_synthetic(ctx, q, int(seed), int(gen_q), int(k_begin), int(k_end), int(n_occ),
+                                                 arr, _addr(eps_occ), _addr(eps_unocc), float(s_div)),
+           "qsgw_chi0_accumulate_synthetic")
