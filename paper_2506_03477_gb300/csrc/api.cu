@@ -15,7 +15,7 @@ using namespace qsgw;
 struct QAcc {
   int n_pb = 0;
   int n_pad = 0;
-  void* acc = nullptr;  // FP64: double2 [L][n_pad][n_pad]; mixed: float4 (double-float complex), same indexing
+  void* acc = nullptr;  // FP64: double2 [L][n_pad][n_pad]; mixed: float2 (hi, lo) planes [L][re|im][n_pad][n_pad]
   size_t bytes = 0;
 };
 

@@ -32,7 +32,7 @@ void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long
                       long long ldw, int L, double2* acc, cudaStream_t s);
 
 // ---- shared epilogues (kernels_epsw.cu)
-// Accumulator formats: FP64 complex (double2) or double-float complex (float4 = re_hi, re_lo, im_hi, im_lo).
+// Accumulator formats: FP64 complex (double2 [l][J][I]) or double-float planes (float2 hi/lo [l][re|im][J][I]).
 enum AccKind { ACC_FP64 = 0, ACC_DF32 = 1 };
 // chi0 = -s * mirror(acc): full Hermitian, diag imag = 0 (out is [L][n][n]).
 void launch_finalize_chi(const void* acc, AccKind kind, int n, int n_pad, int L, double spin, double2* out,

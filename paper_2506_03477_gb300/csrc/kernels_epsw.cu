@@ -10,11 +10,15 @@
 
 namespace qsgw {
 
+// Accumulator element (I, J) of frequency l, `loc` = J * n_pad + I.
+// ACC_FP64: double2 [l][J][I]. ACC_DF32: float2 (hi, lo) planes [l][re|im][J][I].
 template <int KIND>
-__device__ __forceinline__ double2 load_acc(const void* acc, size_t idx) {
-  if (KIND == ACC_FP64) return static_cast<const double2*>(acc)[idx];
-  const float4 f = static_cast<const float4*>(acc)[idx];  // (re_hi, re_lo, im_hi, im_lo)
-  return make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+__device__ __forceinline__ double2 load_acc(const void* acc, int l, size_t loc, int n_pad) {
+  const size_t nn = (size_t)n_pad * n_pad;
+  if (KIND == ACC_FP64) return static_cast<const double2*>(acc)[(size_t)l * nn + loc];
+  const float2* a = static_cast<const float2*>(acc) + (size_t)l * 2 * nn + loc;
+  const float2 re = a[0], im = a[nn];
+  return make_double2((double)re.x + (double)re.y, (double)im.x + (double)im.y);
 }
 
 // MODE 0: out = chi0. MODE 1: out = eps. Grid (n/32 J-blocks, n/32 I-blocks, L), block (32, 8).
@@ -23,16 +27,15 @@ __global__ void readout_kernel(const void* __restrict__ acc, int n, int n_pad, d
                                const double* __restrict__ v, double2* __restrict__ out) {
   __shared__ double2 t[32][33];
   const int bj = blockIdx.x, bi = blockIdx.y, l = blockIdx.z;
-  const size_t abase = (size_t)l * n_pad * n_pad;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool upper = bi <= bj;
   // stage the source block: for an upper/diagonal output block it is acc block (bi, bj) with
   // t[jj][ii] = acc(I, J); for a lower block it is acc block (bj, bi) with t[ii][jj] = acc(J, I).
   for (int y = ty; y < 32; y += 8) {
-    size_t idx;
-    if (upper) idx = abase + (size_t)(bj * 32 + y) * n_pad + (bi * 32 + tx);  // t[y=jj][tx=ii]
-    else       idx = abase + (size_t)(bi * 32 + y) * n_pad + (bj * 32 + tx);  // t[y=ii][tx=jj]
-    t[y][tx] = load_acc<KIND>(acc, idx);
+    size_t loc;
+    if (upper) loc = (size_t)(bj * 32 + y) * n_pad + (bi * 32 + tx);  // t[y=jj][tx=ii]
+    else       loc = (size_t)(bi * 32 + y) * n_pad + (bj * 32 + tx);  // t[y=ii][tx=jj]
+    t[y][tx] = load_acc<KIND>(acc, l, loc, n_pad);
   }
   __syncthreads();
   for (int y = ty; y < 32; y += 8) {

@@ -1,11 +1,523 @@
-// Mixed-precision chi0 assembly (tcgen05). Placeholder until the tensor-core path lands.
+// Mixed-precision chi0 assembly on tcgen05 tensor cores (steps a1-a5).
+//
+//   chi0_IJ(l) = -s * sum_r |w_l(Delta_r)| conj(z_{I,r}) z_{J,r},  |w_l| = 2 Delta/(Delta^2 + omega_l^2)
+//   (Sec. 2, Eq. (polfx) at w = i omega; the accumulator holds the positive-weight sum).
+//
+// Real form: with z = a + i b, stack Re and Im along the MMA M dimension. For 64 rows I of
+// a tile the 128 A-rows are (a_I, b_I) for the real part and (-b_I, a_I) for the imaginary
+// part, paired along K with B-columns (w a_J, w b_J):
+//   Re = sum a_I (w a_J) + b_I (w b_J),   Im = sum a_I (w b_J) - b_I (w a_J).
+// Every frequency is stacked along N: B-column n = l * TJ + j holds w_l(Delta_r) z_{J0+j, r},
+// so one MMA of N = TJ * L <= 256 updates all frequencies from a single A tile in shared memory.
+//
+// Exact leading digit. tcgen05 accumulates FP32 with truncation (round toward zero, measured),
+// so a plain float split would drift. Every operand value x of a chunk of 512 columns is scaled
+// by a power of two 2^e chosen from the chunk maximum (|x 2^e| <= 127) and split as
+//   x 2^e = d0 + d1 + d2 + rem,  d0 = rint(x 2^e) in [-127, 127],  d1 = bf16(x 2^e - d0),
+//   d2 = bf16(x 2^e - d0 - d1),  |rem| <= 2^-19,
+// all three exact BF16 values. Products d0_A d0_B are integers and a chunk sum of them stays
+// below 2^24, so the level-0 TMEM accumulator is exact. The five products of order 1 and 2
+// (d0 d1, d1 d0, d0 d2, d2 d0, d1 d1) share a second accumulator whose truncation error is
+// relative to its own, ~2^-7 smaller, magnitude. Dropped terms are O(2^-25) of the chunk
+// maximum squared, below the FP32 rounding of the inputs. After each chunk both accumulators
+// are scaled by 2^-(eA+eB) (exact) and added into a double-float (2 x FP32) accumulator in
+// global memory; GB300's FP64 rate (~1 TFLOP/s) would make an FP64 read-modify-write here the
+// bottleneck.
+#include <cuda_bf16.h>
+
+#include <vector>
+
 #include "mixed.cuh"
+#include "tc_ptx.cuh"
 
 namespace qsgw {
 
-qsgw_status mixed_accumulate(MixedScratch&, const double2*, long long, int, int, int, int, const double*,
-                             const double*, const OmegaGrid&, float4*, int*, cudaStream_t) {
-  return QSGW_ERR_STATE;
+constexpr int KBR = 16;                   // transition columns per K-block
+constexpr int KBK = 2 * KBR;              // K' per K-block (re/im pairs)
+constexpr int CHR = 512;                  // columns per exact FP32 chunk
+constexpr int KB_PER_CH = CHR / KBR;      // 32
+constexpr int TI = 64;                    // rows I per tile (M = 128)
+constexpr int A_PLANE = 128 * KBK * 2;    // bytes of one digit plane of one A K-block (8 KB)
+constexpr int A_STAGE = 3 * A_PLANE;      // 24 KB
+constexpr int NS = 4;                     // load pipeline stages
+constexpr int NSB = 2;                    // B operand stages
+constexpr int NBG = 256;                  // B-operand / epilogue threads (warps 2..9)
+constexpr int NTHREADS = 64 + NBG;
+constexpr uint32_t TMEM_L12 = 256;        // column of the level-1+2 accumulator
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+// Largest e with m * 2^e <= 127 (m > 0), so that the leading digit fits in [-127, 127].
+__device__ __forceinline__ int scale_exp(float m) {
+  if (!(m > 0.f) || !isfinite(m)) return 0;
+  int E;
+  const float f = frexpf(m, &E);  // m = f 2^E, f in [0.5, 1)
+  int e = 7 - E;
+  if (f > 127.f / 128.f) e -= 1;
+  return max(-120, min(120, e));
+}
+__device__ __forceinline__ float exp2i(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((e + 127) << 23);
+}
+
+// Three BF16-exact digits of t (|t| <= 127.5): d0 = rint(t) (integer), then the remainder split
+// twice by round-to-nearest BF16. t - d0 and u - d1 are exact in FP32 (Sterbenz).
+__device__ __forceinline__ void digits3(float t, float& d0, float& d1, float& d2) {
+  d0 = rintf(t);
+  const float u = t - d0;
+  d1 = __bfloat162float(__float2bfloat16_rn(u));
+  const float u2 = u - d1;
+  d2 = __bfloat162float(__float2bfloat16_rn(u2));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// ------------------------------------------------------------------ prep: columns
+// One CTA per chunk of 512 columns: Delta, domain check, |w_l| in FP32 ([r][l]), and the
+// per-chunk maximum of each |w_l| (for the B-operand scale bound).
+__global__ void __launch_bounds__(CHR) prep_cols_kernel(const double* __restrict__ eo, const double* __restrict__ eu,
+                                                        int n_unocc, long long K, OmegaGrid g, float* __restrict__ wst,
+                                                        float* __restrict__ wmax, int* d_err) {
+  __shared__ float red[CHR / 32][kMaxOmega];
+  const int c = blockIdx.x, t = threadIdx.x, L = g.L;
+  const long long r = (long long)c * CHR + t;
+  bool ok = false;
+  float d = 0.f;
+  if (r < K) {
+    const int n = (int)(r / n_unocc), m = (int)(r % n_unocc);
+    const double dd = eu[m] - eo[n];
+    ok = (dd > 0.0) && isfinite(dd);
+    if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
+    d = (float)dd;
+  }
+  for (int l = 0; l < L; ++l) {
+    float w = ok ? 2.f * d / (d * d + g.w2f[l]) : 0.f;
+    wst[r * L + l] = w;
+    for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
+    if ((t & 31) == 0) red[t >> 5][l] = w;
+  }
+  __syncthreads();
+  if (t < L) {
+    float m = 0.f;
+    for (int w = 0; w < CHR / 32; ++w) m = fmaxf(m, red[w][t]);
+    wmax[c * L + t] = m;
+  }
+}
+
+// ------------------------------------------------------------------ prep: rows
+// One CTA per (chunk, 64-row tile): chunk maximum of max(|Re z|, |Im z|) per row, its exponent,
+// the A-operand digit planes written as the exact shared-memory image of each K-block
+// ([plane][k-group 4][row-group 16][8 rows][8 K'] BF16, canonical no-swizzle K-major), and the
+// FP32 copy of Z laid out per J-tile and K-block ([jt][kb][16 r][TJ] float2) for the B side.
+__global__ void __launch_bounds__(256) prep_rows_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
+                                                        long long K, int n_pad, int n_kb, int TJ, int n_jt,
+                                                        uint8_t* __restrict__ aplanes, float2* __restrict__ braw,
+                                                        float* __restrict__ zmax, int* __restrict__ expA) {
+  __shared__ float red[4][TI];
+  const int c = blockIdx.x, it = blockIdx.y;
+  const int il = threadIdx.x & (TI - 1), q = threadIdx.x >> 6;
+  const int I = it * TI + il;
+  const bool rowok = I < n_pb;
+  float m = 0.f;
+  for (int jc = q; jc < CHR; jc += 4) {
+    const long long r = (long long)c * CHR + jc;
+    if (rowok && r < K) {
+      const double2 z = Z[I + r * ldz];
+      m = fmaxf(m, fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
+    }
+  }
+  red[q][il] = m;
+  __syncthreads();
+  m = fmaxf(fmaxf(red[0][il], red[1][il]), fmaxf(red[2][il], red[3][il]));
+  const int eA = scale_exp(m);
+  if (q == 0) {
+    zmax[(size_t)c * n_pad + I] = m;
+    expA[(size_t)c * n_pad + I] = eA;
+  }
+  const float sA = exp2i(eA);
+  const int jt = I / TJ, jj = I % TJ;
+  const bool braw_ok = jt < n_jt;
+  for (int kbl = 0; kbl < KB_PER_CH; ++kbl) {
+    const int kb = c * KB_PER_CH + kbl;
+    float a[4], b[4];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const long long r = (long long)kb * KBR + q * 4 + rr;
+      double2 z = make_double2(0.0, 0.0);
+      if (rowok && r < K) z = Z[I + r * ldz];
+      a[rr] = (float)z.x;
+      b[rr] = (float)z.y;
+      if (braw_ok) braw[(((size_t)jt * n_kb + kb) * KBR + q * 4 + rr) * TJ + jj] = make_float2(a[rr], b[rr]);
+    }
+    float da[3][4], db[3][4];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      digits3(a[rr] * sA, da[0][rr], da[1][rr], da[2][rr]);
+      digits3(b[rr] * sA, db[0][rr], db[1][rr], db[2][rr]);
+    }
+    uint8_t* base = aplanes + ((size_t)it * n_kb + kb) * A_STAGE + q * 2048;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      uint4 re, im;  // Re row: (a, b) pairs; Im row: (-b, a) pairs
+      re.x = pack_bf16(da[p][0], db[p][0]);
+      re.y = pack_bf16(da[p][1], db[p][1]);
+      re.z = pack_bf16(da[p][2], db[p][2]);
+      re.w = pack_bf16(da[p][3], db[p][3]);
+      im.x = pack_bf16(-db[p][0], da[p][0]);
+      im.y = pack_bf16(-db[p][1], da[p][1]);
+      im.z = pack_bf16(-db[p][2], da[p][2]);
+      im.w = pack_bf16(-db[p][3], da[p][3]);
+      const int mre = il, mim = TI + il;
+      *reinterpret_cast<uint4*>(base + p * A_PLANE + (mre >> 3) * 128 + (mre & 7) * 16) = re;
+      *reinterpret_cast<uint4*>(base + p * A_PLANE + (mim >> 3) * 128 + (mim & 7) * 16) = im;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ main tensor-core kernel
+struct MainArgs {
+  const uint8_t* aplanes;
+  const float2* braw;
+  const float* wst;
+  const float* zmax;
+  const int* expA;
+  const float* wmax;
+  const int2* tiles;
+  float2* acc;  // [l][part][J][I] (hi, lo)
+  int n_pb, n_pad, L, TJ, N, n_kb, n_jt;
+  uint32_t idesc;
+  int* d_err;
+};
+
+__device__ __forceinline__ void df_add(float2& v, float x) {
+  const float s = v.x + x;
+  const float bb = s - v.x;
+  const float e = (v.x - (s - bb)) + (x - bb);
+  v.x = s;
+  v.y += e;
+}
+
+__host__ __device__ constexpr size_t main_smem_bytes(int N, int TJ, int L) {
+  return 1024 + (size_t)NS * A_STAGE + (size_t)NSB * 3 * 64 * N + (size_t)NS * KBR * TJ * 8 +
+         (size_t)NS * KBR * L * 4 + 256 * 4 * 2 + 32 * 8 + 64;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int N = p.N, TJ = p.TJ, L = p.L;
+  const int BPLANE = 64 * N;  // bytes of one B digit plane of one K-block
+  const int BSTAGE = 3 * BPLANE;
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + NS * A_STAGE;
+  float2* sRaw = reinterpret_cast<float2*>(sB + NSB * BSTAGE);
+  float* sW = reinterpret_cast<float*>(sRaw + NS * KBR * TJ);
+  float* sScale = sW + NS * KBR * L;
+  int* sExpB = reinterpret_cast<int*>(sScale + 256);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sExpB + 256);
+  uint64_t* full = bars;             // [NS]   producer -> MMA, B-gen (bulk copies landed)
+  uint64_t* empty = full + NS;       // [NS]   MMA commit + 8 B-gen warps -> producer
+  uint64_t* bfull = empty + NS;      // [NSB]  8 B-gen warps -> MMA
+  uint64_t* bempty = bfull + NSB;    // [NSB]  MMA commit -> B-gen
+  uint64_t* accfull = bempty + NSB;  // MMA commit at chunk end -> epilogue
+  uint64_t* accempty = accfull + 1;  // 8 epilogue warps -> MMA
+  uint64_t* finbar = accempty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(finbar + 1);
+  int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [3]: B-gen K-block slots (parity) + epilogue
+  int* abortP = abortB + 3;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1 + NBG / 32);
+    }
+    for (int s = 0; s < NSB; ++s) {
+      mbar_init(&bfull[s], NBG / 32);
+      mbar_init(&bempty[s], 1);
+    }
+    mbar_init(accfull, 1);
+    mbar_init(accempty, NBG / 32);
+    mbar_init(finbar, 1);
+    abortB[0] = abortB[1] = abortB[2] = 0;
+    *abortP = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int2 tile = p.tiles[blockIdx.x];
+  const int it = tile.x, jt = tile.y;
+  const int n_kb = p.n_kb;
+
+  if (warp == 0) {
+    // ---------------- producer: bulk copies of the A digit planes, raw B values and weights
+    if (lane == 0) {
+      const uint32_t raw_bytes = KBR * TJ * 8, w_bytes = KBR * L * 4;
+      int issued = 0;
+      for (int kb = 0; kb < n_kb; ++kb) {
+        const int s = kb % NS, round = kb / NS;
+        if (kb >= NS && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitNs)) {
+          *abortP = 1;
+          atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+          break;
+        }
+        mbar_arrive_expect_tx(&full[s], A_STAGE + raw_bytes + w_bytes);
+        bulk_g2s(sA + s * A_STAGE, p.aplanes + ((size_t)it * n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
+        bulk_g2s(sRaw + s * KBR * TJ, p.braw + ((size_t)jt * n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
+        bulk_g2s(sW + s * KBR * L, p.wst + (size_t)kb * KBR * L, w_bytes, &full[s]);
+        issued = kb + 1;
+      }
+      // never leave a bulk copy in flight into shared memory at exit
+      for (int kb = (issued > NS ? issued - NS : 0); kb < issued; ++kb)
+        mbar_wait_bounded(&full[kb % NS], (kb / NS) & 1, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (one thread)
+    if (lane == 0) {
+      const uint32_t idesc = p.idesc;
+      for (int kb = 0; kb < n_kb; ++kb) {
+        const int s = kb % NS, sb = kb % NSB, kbl = kb % KB_PER_CH;
+        bool ok = mbar_wait_bounded(&full[s], (kb / NS) & 1, kWaitNs);
+        ok = ok && mbar_wait_bounded(&bfull[sb], (kb / NSB) & 1, kWaitNs);
+        if (ok && kbl == 0 && kb > 0) ok = mbar_wait_bounded(accempty, ((kb / KB_PER_CH) - 1) & 1, kWaitNs);
+        if (!ok) {
+          *abortP = 1;
+          atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(sA + s * A_STAGE), b_base = smem_u32(sB + sb * BSTAGE);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint32_t ao = a_base + ks * 4096, bo = b_base + ks * 32 * N;
+          const uint64_t a0 = make_smem_desc(ao, 2048, 128, 0);
+          const uint64_t a1 = make_smem_desc(ao + A_PLANE, 2048, 128, 0);
+          const uint64_t a2 = make_smem_desc(ao + 2 * A_PLANE, 2048, 128, 0);
+          const uint64_t b0 = make_smem_desc(bo, 16 * N, 128, 0);
+          const uint64_t b1 = make_smem_desc(bo + BPLANE, 16 * N, 128, 0);
+          const uint64_t b2 = make_smem_desc(bo + 2 * BPLANE, 16 * N, 128, 0);
+          const uint32_t acc_in = (kbl == 0 && ks == 0) ? 0u : 1u;
+          mma_bf16(tmem, a0, b0, idesc, acc_in);
+          mma_bf16(tmem + TMEM_L12, a0, b1, idesc, acc_in);
+          mma_bf16(tmem + TMEM_L12, a1, b0, idesc, 1u);
+          mma_bf16(tmem + TMEM_L12, a0, b2, idesc, 1u);
+          mma_bf16(tmem + TMEM_L12, a2, b0, idesc, 1u);
+          mma_bf16(tmem + TMEM_L12, a1, b1, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&bempty[sb]);
+        if (kbl == KB_PER_CH - 1) mma_commit(accfull);
+      }
+      // drain: all issued MMAs complete before TMEM is released
+      mma_commit(finbar);
+      mbar_wait_bounded(finbar, 0, kWaitNs);
+    }
+  } else {
+    // ---------------- B operand generation (scaled digits, all frequencies) + chunk epilogue
+    const int bt = tid - 64;
+    const int quarter = warp & 3;             // TMEM lane quarter this warp may access
+    const int wg = (warp - 2) >> 2;           // column half handled in the epilogue
+    const int m_row = quarter * 32 + lane;    // accumulator lane = A row
+    const int part = m_row / TI, I = it * TI + (m_row % TI);
+    for (int kb = 0; kb < n_kb; ++kb) {
+      const int s = kb % NS, sb = kb % NSB, kbl = kb % KB_PER_CH, c = kb / KB_PER_CH;
+      if (kbl == 0) {  // B scales of this chunk: 2^eB with eB from max_r |w_l| * max_r |z_J|
+        for (int n = bt; n < N; n += NBG) {
+          const int l = n / TJ, J = jt * TJ + (n % TJ);
+          const float zm = J < p.n_pb ? p.zmax[(size_t)c * p.n_pad + J] : 0.f;
+          const int e = scale_exp(p.wmax[c * L + l] * zm);
+          sExpB[n] = e;
+          sScale[n] = exp2i(e);
+        }
+      }
+      bool ok = mbar_wait_bounded(&full[s], (kb / NS) & 1, kWaitNs);
+      if (ok && kb >= NSB) ok = mbar_wait_bounded(&bempty[sb], ((kb / NSB) - 1) & 1, kWaitNs);
+      // a slot per K-block parity: a thread one K-block ahead never writes the slot others still read
+      if (!ok) abortB[kb & 1] = 1;
+      named_bar_sync(1, NBG);  // also orders the scale-table writes above
+      if (abortB[kb & 1]) break;
+      const float2* raw = sRaw + s * KBR * TJ;
+      const float* ws = sW + s * KBR * L;
+      uint8_t* bdst = sB + sb * BSTAGE;
+      for (int item = bt; item < 4 * N; item += NBG) {
+        const int n = item % N, g = item / N;
+        const int l = n / TJ, j = n % TJ;
+        const bool jok = jt * TJ + j < p.n_pb;
+        const float sc = sScale[n];
+        float xr[4], xi[4];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          const int rl = g * 4 + rr;
+          const float2 z = jok ? raw[rl * TJ + j] : make_float2(0.f, 0.f);
+          const float ww = ws[rl * L + l] * sc;
+          xr[rr] = ww * z.x;
+          xi[rr] = ww * z.y;
+        }
+        float d[3][8];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          digits3(xr[rr], d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
+          digits3(xi[rr], d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
+        }
+        const int off = g * 16 * N + (n >> 3) * 128 + (n & 7) * 16;
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+          uint4 v;
+          v.x = pack_bf16(d[pl][0], d[pl][1]);
+          v.y = pack_bf16(d[pl][2], d[pl][3]);
+          v.z = pack_bf16(d[pl][4], d[pl][5]);
+          v.w = pack_bf16(d[pl][6], d[pl][7]);
+          *reinterpret_cast<uint4*>(bdst + pl * BPLANE + off) = v;
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bfull[sb]);
+        mbar_arrive(&empty[s]);
+      }
+      if (kbl == KB_PER_CH - 1) {
+        // ------------- chunk epilogue: TMEM -> registers -> scaled -> double-float global accumulator
+        ok = mbar_wait_bounded(accfull, c & 1, kWaitNs);
+        if (!ok) abortB[2] = 1;
+        named_bar_sync(1, NBG);
+        if (abortB[2]) break;
+        tc_fence_after();
+        const int eA = p.expA[(size_t)c * p.n_pad + I];
+        const bool iok = I < p.n_pb;
+        const int half = N / 2;
+        for (int col0 = wg * half; col0 < (wg + 1) * half; col0 += 8) {
+          uint32_t r0[8], r1[8];
+          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
+          tmem_ld_x8(ta, r0);
+          tmem_ld_x8(ta + TMEM_L12, r1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n % TJ);
+            if (iok && J < p.n_pb) {
+              const float sc = exp2i(-(eA + sExpB[n]));
+              float2* ap = p.acc + (((size_t)(l * 2 + part) * p.n_pad + J) * p.n_pad + I);
+              float2 v = *ap;
+              df_add(v, __uint_as_float(r0[jj]) * sc);
+              df_add(v, __uint_as_float(r1[jj]) * sc);
+              *ap = v;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(accempty);
+        named_bar_sync(1, NBG);  // scale table of this chunk no longer needed
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+// J columns per tile: the widest TJ <= 32 with N = TJ * L <= 256 and N % 16 == 0 (MMA shape
+// rule for M = 128). TJ <= 32 bounds the raw-operand stages in shared memory.
+static int tile_width(int L) {
+  for (int t = (256 / L < 32 ? 256 / L : 32); t >= 1; --t)
+    if ((t * L) % 16 == 0) return t;
+  return 0;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, int n_pb, int n_pad, int n_occ,
+                             int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
+                             int* d_err, cudaStream_t stream) {
+  const int L = g.L, TJ = tile_width(L), N = TJ * L;
+  if (TJ < 1 || N < 16 || N > 256) return QSGW_ERR_ARG;
+  const long long K = (long long)n_occ * n_unocc;
+  const int n_ch = (int)((K + CHR - 1) / CHR), n_kb = n_ch * KB_PER_CH;
+  const int n_it = n_pad / TI, n_jt = (n_pb + TJ - 1) / TJ;
+
+  const size_t sz_a = (size_t)n_it * n_kb * A_STAGE;
+  const size_t sz_raw = (size_t)n_jt * n_kb * KBR * TJ * sizeof(float2);
+  const size_t sz_w = (size_t)n_kb * KBR * L * sizeof(float);
+  const size_t sz_zmax = (size_t)n_ch * n_pad * sizeof(float);
+  const size_t sz_exp = (size_t)n_ch * n_pad * sizeof(int);
+  const size_t sz_wmax = (size_t)n_ch * L * sizeof(float);
+  const size_t o_raw = align256(sz_a), o_w = o_raw + align256(sz_raw), o_zmax = o_w + align256(sz_w);
+  const size_t o_exp = o_zmax + align256(sz_zmax), o_wmax = o_exp + align256(sz_exp);
+  const size_t total = o_wmax + align256(sz_wmax);
+  if (s.planes_cap < total) {
+    if (s.planes) cudaFree(s.planes);
+    s.planes = nullptr;
+    s.planes_cap = 0;
+    if (cudaMalloc(&s.planes, total) != cudaSuccess) return QSGW_ERR_NOMEM;
+    s.planes_cap = total;
+  }
+  // tile list (upper triangle: some J >= some I), rebuilt when the shape changes
+  if (s.tiles_key_n != n_pb || s.tiles_key_tj != TJ) {
+    std::vector<int2> tl;
+    for (int it = 0; it < n_it; ++it)
+      for (int jt = 0; jt < n_jt; ++jt)
+        if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) tl.push_back(make_int2(it, jt));
+    if (s.aux) cudaFree(s.aux);
+    s.aux = nullptr;
+    if (cudaMalloc(&s.aux, tl.size() * sizeof(int2)) != cudaSuccess) return QSGW_ERR_NOMEM;
+    if (cudaMemcpy(s.aux, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return QSGW_ERR_CUDA;
+    s.n_tiles = (int)tl.size();
+    s.tiles_key_n = n_pb;
+    s.tiles_key_tj = TJ;
+  }
+  uint8_t* base = static_cast<uint8_t*>(s.planes);
+  auto* aplanes = base;
+  auto* braw = reinterpret_cast<float2*>(base + o_raw);
+  auto* wst = reinterpret_cast<float*>(base + o_w);
+  auto* zmax = reinterpret_cast<float*>(base + o_zmax);
+  auto* expA = reinterpret_cast<int*>(base + o_exp);
+  auto* wmax = reinterpret_cast<float*>(base + o_wmax);
+
+  prep_cols_kernel<<<n_ch, CHR, 0, stream>>>(eo, eu, n_unocc, K, g, wst, wmax, d_err);
+  prep_rows_kernel<<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt, aplanes, braw,
+                                                          zmax, expA);
+  MainArgs a;
+  a.aplanes = aplanes;
+  a.braw = braw;
+  a.wst = wst;
+  a.zmax = zmax;
+  a.expA = expA;
+  a.wmax = wmax;
+  a.tiles = static_cast<const int2*>(s.aux);
+  a.acc = reinterpret_cast<float2*>(acc);
+  a.n_pb = n_pb;
+  a.n_pad = n_pad;
+  a.L = L;
+  a.TJ = TJ;
+  a.N = N;
+  a.n_kb = n_kb;
+  a.n_jt = n_jt;
+  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
+  a.d_err = d_err;
+  const size_t smem = main_smem_bytes(N, TJ, L);
+  if (!s.attr_set) {
+    if (cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+        cudaSuccess)
+      return QSGW_ERR_CUDA;
+    s.attr_set = true;
+  }
+  herk_mixed_kernel<<<s.n_tiles, NTHREADS, smem, stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
 }
 
 void mixed_free(MixedScratch& s) {
