@@ -1,0 +1,398 @@
+"""Benchmark of the chi0 -> eps -> W hot path on GB300.
+
+Workload: the medium synthetic workload (n_pb = 1500, 64 k-points x 40 occupied x 400
+unoccupied = 1,024,000 transition columns, 12 imaginary frequencies, spin factor 2, Philox
+inputs). One step = one pass of the whole path: reset, accumulate every k-point (prep +
+tensor-core HERK), chi0 readout, eps, FP64 Cholesky inverse and W.
+
+Metric: algorithmic chi0 TFLOP/s, F = 4 K n_pb (n_pb + 1) L per step, over the whole step time
+(eps/W included), mixed precision (the default `--prec mixed`). The FP64 form is measured on a
+2-k-point sample of the same Z (GB300 FP64 runs at ~1 TFLOP/s) and reported beside it.
+
+`--impl reference` times the FP64 CPU oracle (test infrastructure) on a bounded sample of the
+same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import MEDIUM, coulomb_v, eps_occ, eps_unocc  # noqa: E402
+
+WL = MEDIUM
+N_PB, N_K, N_OCC, N_UNOCC, L = WL.n_pb(0), WL.n_k, WL.n_occ, 400, WL.n_omega
+K_COLS = N_K * N_OCC * N_UNOCC
+F_STEP = 4.0 * K_COLS * N_PB * (N_PB + 1) * L
+CONFIG_NAME = "medium chi0+W: n_pb=1500, n_k=64, n_occ=40, n_unocc=400 (K=1,024,000), 12 imaginary frequencies"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("bf16_tflops_sustained", 1698.0), d.get("bf16_tflops", 1899.6), d.get("hbm_gbs", 6789.3), "measured"
+    return 1700.0, 1900.0, 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        under_load = [s for s, p in zip(sm, power) if p > 0.5 * max(power)] or sm
+        return {"sm_mhz": statistics.median(under_load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, dev_index):
+    import torch
+    from paper_2506_03477_gb300 import native as N
+
+    torch.cuda.set_device(dev_index)
+    dev = torch.device("cuda", dev_index)
+    stream = torch.cuda.Stream(dev)
+    gen_q = rank  # weak scaling: every rank assembles its own q-point
+    prec = N.QSGW_MIXED_BF16X3 if args.prec == "mixed" else N.QSGW_FP64
+
+    # inputs resident in HBM (generated on the device, untimed)
+    ncol = N_OCC * N_UNOCC
+    nk = args.k_points
+    Z = torch.empty((nk, ncol, N_PB), dtype=torch.complex128, device=dev)
+    eo = torch.from_numpy(np.stack([eps_occ(WL.seed, gen_q, k, N_OCC) for k in range(N_K)])).to(dev)
+    eu = torch.from_numpy(np.stack([eps_unocc(WL.seed, gen_q, k, N_UNOCC) for k in range(N_K)])).to(dev)
+    v = torch.from_numpy(coulomb_v(WL.seed, gen_q, N_PB)).to(dev)
+    with torch.cuda.stream(stream):
+        for k in range(nk):
+            N.qsgw_synth_z(WL.seed, gen_q, k, N_PB, N_OCC, N_UNOCC, WL.s_div, Z[k], N_PB, stream=stream)
+    chi = torch.empty((L, N_PB, N_PB), dtype=torch.complex128, device=dev)
+    W = torch.empty_like(chi)
+    torch.cuda.synchronize(dev)
+
+    ctx = N.qsgw_chi0_init([N_PB], WL.omega, WL.spin, prec, stream=stream)
+    acc_events = []
+
+    def step(record=False):
+        N.qsgw_chi0_reset(ctx, 0)
+        for k in range(nk):
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            N.qsgw_chi0_accumulate(ctx, 0, Z[k], N_PB, N_OCC, N_UNOCC, eo[k], eu[k], WL.omega)
+            if record:
+                e1.record(stream)
+                acc_events.append((e0, e1))
+        N.qsgw_chi0_finalize(ctx, 0, chi)
+        N.qsgw_eps_inv(ctx, 0, v, W, n_omega=L)
+
+    launches_per_step = nk * 3 + 1 + 2  # prep_cols, prep_rows, HERK per k; readout; eps + W kernels
+    if prec == N.QSGW_FP64:
+        launches_per_step = nk * 2 + 3
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    with ClockSampler(dev_index) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms_total = t0.elapsed_time(t1)
+    ms_step = ms_total / args.steps
+    ms_step = max_over_ranks(ms_step, world)
+    acc_ms = [a.elapsed_time(b) for a, b in acc_events]
+
+    # FP64 form of the same path on a 2-k-point sample (TFLOP/s is intensive)
+    fp64 = None
+    if args.prec == "mixed" and not args.skip_fp64:
+        ctx64 = N.qsgw_chi0_init([N_PB], WL.omega, WL.spin, N.QSGW_FP64, stream=stream)
+        ks = [0, 1]
+        for k in ks:  # warm-up
+            N.qsgw_chi0_accumulate(ctx64, 0, Z[k], N_PB, N_OCC, N_UNOCC, eo[k], eu[k], WL.omega)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in ks:
+            N.qsgw_chi0_accumulate(ctx64, 0, Z[k], N_PB, N_OCC, N_UNOCC, eo[k], eu[k], WL.omega)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        N.qsgw_chi0_destroy(ctx64)
+        f_s = 4.0 * len(ks) * ncol * N_PB * (N_PB + 1) * L
+        fp64_ms = a.elapsed_time(b)
+        fp64 = {"tflops": f_s / (fp64_ms * 1e-3) / 1e12, "sample": f"chi0 accumulation of {len(ks)} of 64 k-points",
+                "ms": fp64_ms}
+
+    # end to end through the C ABI with host buffers (pinned): Z streamed in by the library
+    e2e = None
+    if not args.skip_e2e:
+        Zh = torch.empty(Z.shape, dtype=Z.dtype, pin_memory=True)
+        Zh.copy_(Z)
+        eoh, euh = eo.cpu().numpy(), eu.cpu().numpy()
+        chi_h = torch.empty(chi.shape, dtype=chi.dtype, pin_memory=True)
+        W_h = torch.empty(W.shape, dtype=W.dtype, pin_memory=True)
+        del Z
+        torch.cuda.empty_cache()
+
+        def e2e_step():
+            N.qsgw_chi0_reset(ctx, 0)
+            for k in range(nk):
+                N.qsgw_chi0_accumulate(ctx, 0, Zh[k], N_PB, N_OCC, N_UNOCC, eoh[k], euh[k], WL.omega)
+            N.qsgw_chi0_finalize(ctx, 0, chi)
+            N.qsgw_eps_inv(ctx, 0, v, W, n_omega=L)
+            with torch.cuda.stream(stream):
+                chi_h.copy_(chi, non_blocking=True)
+                W_h.copy_(W, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        barrier(world)
+        t = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 3))
+        for _ in range(n_e2e):
+            e2e_step()
+        e2e_s = (time.perf_counter() - t) / n_e2e
+        e2e_s = max_over_ranks(e2e_s, world)
+        h2d = Zh.numel() * 16 + (eoh.size + euh.size) * 8
+        d2h = 2 * chi.numel() * 16
+        e2e = {"value": world * F_STEP * nk / N_K / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+    N.qsgw_chi0_destroy(ctx)
+
+    res = dict(ms_step=ms_step, acc_ms=acc_ms, fp64=fp64, e2e=e2e, clocks=clk.summary(),
+               launches=launches_per_step * args.steps, chi=chi)
+    return res
+
+
+# ------------------------------------------------------------------ oracle (CPU) legs
+def oracle_inputs(rows):
+    """Rows of Z (host generator) and Delta for the sampled chi0 block."""
+    import oracle
+    from synthetic import z_rows
+
+    ZS = z_rows(WL.seed, 0, rows, N_K, N_OCC, lambda k: N_UNOCC, WL.s_div)
+    d = np.concatenate([oracle.delta(eps_occ(WL.seed, 0, k, N_OCC), eps_unocc(WL.seed, 0, k, N_UNOCC))[0]
+                        for k in range(N_K)])
+    return ZS, d
+
+
+def oracle_block(ZS, d):
+    """Time the FP64 oracle on chi0[rows, rows] over all 1,024,000 columns and 12 frequencies."""
+    import oracle
+
+    oracle.build()
+    t = time.perf_counter()
+    ref = oracle.chi0_rows(ZS, ZS, d, WL.omega, WL.spin)
+    sec = time.perf_counter() - t
+    flops = 8.0 * K_COLS * L * ZS.shape[0] * ZS.shape[0]
+    return ref, sec, flops
+
+
+def sample_rows(n):
+    rng = np.random.default_rng(5)
+    return np.unique(np.concatenate([[0, 1499], rng.choice(N_PB, n - 2, replace=False)]))[:n]
+
+
+def cpu_baseline(chi_gpu=None, n_rows=48):
+    rows = sample_rows(n_rows)
+    ref, sec, flops = oracle_block(*oracle_inputs(rows))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"value": flops / sec / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+           "sample": f"FP64 oracle chi0 block {len(rows)}x{len(rows)} rows/cols x 1,024,000 columns x 12 frequencies "
+                     f"({flops:.3g} algorithmic flops, {sec:.1f} s)"}
+    if chi_gpu is not None:
+        got = chi_gpu.cpu().numpy().transpose(0, 2, 1)[:, rows][:, :, rows]
+        err = max(np.linalg.norm(got[l] - ref[l]) / np.linalg.norm(ref[l]) for l in range(L))
+        out["check"] = {"chi0_block_rel_fro_max_over_omega": float(err)}
+    return out
+
+
+# ------------------------------------------------------------------ distributed helpers
+_PG = None
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier(group=_PG)
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=_PG)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--k-points", type=int, default=64,
+                    help="k-points per step (profiling aid for small captures; bench lines use all 64)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    global _PG
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+        _PG = dist.group.WORLD
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle  # noqa: F401
+        rows = sample_rows(24)
+        ZS, d = oracle_inputs(rows)
+        secs, flops = [], 0.0
+        for _ in range(args.warmup):
+            oracle_block(ZS, d)
+        for _ in range(args.steps):
+            _, s, flops = oracle_block(ZS, d)
+            secs.append(s)
+        sec = statistics.mean(secs)
+        val = flops / sec / 1e12
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        sample = (f"FP64 oracle chi0 block {len(rows)}x{len(rows)} x 1,024,000 columns x 12 frequencies per step "
+                  f"({flops:.3g} algorithmic flops)")
+        print(json.dumps({"impl": "reference", "metric": metric_name(), "value": val, "unit": "TFLOP/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": config(args),
+                          "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    res = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    sustained, burst, hbm, src = peaks()
+    f_step = F_STEP * args.k_points / N_K
+    value = world * f_step / (res["ms_step"] * 1e-3) / 1e12
+    acc = res["acc_ms"]
+    acc_avg = statistics.mean(acc)
+    f_launch = F_STEP / N_K
+    achieved = f_launch / (acc_avg * 1e-3) / 1e12
+    issued = issued_mma_flops_per_call() if args.prec == "mixed" else None
+    roof = {"bound": "tensor" if args.prec == "mixed" else "alu", "kernel": "herk_mixed_kernel (+ prep kernels in the timed call)",
+            "achieved": achieved, "peak": sustained, "unit": "TFLOP/s", "frac": achieved / sustained,
+            "peak_source": f"{src} bf16 sustained", "traffic": None,
+            "note": "achieved = algorithmic chi0 flops per accumulate call / CUDA-event duration of the call"}
+    if issued:
+        roof["tensor_pipe_issued_tflops"] = issued / (acc_avg * 1e-3) / 1e12
+        roof["tensor_pipe_frac"] = roof["tensor_pipe_issued_tflops"] / sustained
+    out = {"metric": metric_name(), "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16x3-exact-digit" if args.prec == "mixed" else "f64", "data": "synthetic",
+           "config": config(args), "roofline": roof, "gpu_launches": res["launches"], "clocks": res["clocks"],
+           "e2e": res["e2e"]}
+    if res["fp64"]:
+        out["fp64"] = res["fp64"]
+        out["mixed_over_fp64"] = achieved / res["fp64"]["tflops"]
+    out["chi0_only_tflops"] = achieved
+    out["ms_chi0_per_step"] = acc_avg * args.k_points
+    out["ms_eps_w_per_step"] = res["ms_step"] - acc_avg * args.k_points
+    if args.k_points != N_K:
+        out["note"] = f"profiling case: {args.k_points} of {N_K} k-points per step (not a bench line)"
+    if not args.skip_cpu and args.k_points == N_K:
+        out["cpu_baseline"] = cpu_baseline(res["chi"])
+    print(json.dumps(out))
+
+
+def issued_mma_flops_per_call():
+    """BF16 MMA flops one accumulate call issues (same tiling rules as the library)."""
+    TJ = next(t for t in range(min(256 // L, 32), 0, -1) if (t * L) % 16 == 0)
+    n = TJ * L
+    n_pad = (N_PB + 63) // 64 * 64
+    n_it, n_jt = n_pad // 64, (N_PB + TJ - 1) // TJ
+    tiles = sum(1 for it in range(n_it) for jt in range(n_jt) if jt * TJ + TJ - 1 >= it * 64 and it * 64 < N_PB)
+    n_kb = (N_OCC * N_UNOCC + 511) // 512 * 32
+    return tiles * n_kb * 2 * 6 * (2.0 * 128 * n * 16)
+
+
+def metric_name():
+    return "chi0(q,iw) assembly TFLOP/s on 1 GB300: mixed vs FP64 at <=1e-6 rel. err"
+
+
+def config(args):
+    return {"workload": CONFIG_NAME, "precision": args.prec, "n_pb": N_PB, "K": K_COLS, "n_omega": L,
+            "flops_per_step": F_STEP, "step": "reset + 64 accumulate calls + chi0 readout + eps + Cholesky inverse + W",
+            "l2": "inputs (24.6 GB of Z) larger than L2; no flush", "parallelism": "replicas over q (weak)"}
+
+
+if __name__ == "__main__":
+    main()
