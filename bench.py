@@ -380,8 +380,8 @@ def issued_mma_flops_per_call():
     n_pad = (N_PB + 63) // 64 * 64
     n_it, n_jt = n_pad // 64, (N_PB + TJ - 1) // TJ
     tiles = sum(1 for it in range(n_it) for jt in range(n_jt) if jt * TJ + TJ - 1 >= it * 64 and it * 64 < N_PB)
-    n_kb = (N_OCC * N_UNOCC + 511) // 512 * 32
-    return tiles * n_kb * 2 * 6 * (2.0 * 128 * n * 16)
+    n_kb = (N_OCC * N_UNOCC + 1023) // 1024 * 64
+    return tiles * n_kb * 2 * 8 * (2.0 * 128 * n * 16)
 
 
 def metric_name():

@@ -11,20 +11,19 @@
 // so one MMA of N = TJ * L <= 256 updates all frequencies from a single A tile in shared memory.
 //
 // Exact leading digit. tcgen05 accumulates FP32 with truncation (round toward zero, measured),
-// so a plain float split would drift. Every operand value x of a chunk of 512 columns is scaled
-// by a power of two 2^e chosen from the chunk maximum (|x 2^e| <= 127) and split as
-//   x 2^e = d0 + d1 + d2 + rem,  d0 = rint(x 2^e) in [-127, 127],  d1 = bf16(x 2^e - d0),
+// so a plain float split would drift. Every operand value x of a chunk of 1024 columns is scaled
+// by a power of two 2^e chosen from the chunk maximum (|x 2^e| <= 90) and split as
+//   x 2^e = d0 + d1 + d2 + rem,  d0 = rint(x 2^e) in [-90, 90],  d1 = bf16(x 2^e - d0),
 //   d2 = bf16(x 2^e - d0 - d1),  |rem| <= 2^-19,
 // all three exact BF16 values. Products d0_A d0_B are integers and a chunk sum of them stays
-// below 2^24, so the level-0 TMEM accumulator is exact. The five products of order 1 and 2
-// (d0 d1, d1 d0, d0 d2, d2 d0, d1 d1) share a second accumulator whose truncation error is
-// relative to its own, ~2^-7 smaller, magnitude. Dropped terms are O(2^-25) of the chunk
-// maximum squared, below the FP32 rounding of the inputs. After each chunk both accumulators
+// below 2 * 1024 * 90^2 < 2^24, so the level-0 TMEM accumulator is exact. The seven products
+// d0 d1, d1 d0, d0 d2, d2 d0, d1 d1, d1 d2, d2 d1 share a second accumulator whose truncation
+// error is relative to its own, ~2^-6 smaller, magnitude. The dropped d2 d2 term and the
+// remainders are ~2^-23 of a typical product, at the level of the FP32 rounding of the inputs
+// (d1 d2 alone would be ~2^-20 of a typical product, which is why it is kept). After each chunk both accumulators
 // are scaled by 2^-(eA+eB) (exact) and added into a double-float (2 x FP32) accumulator in
 // global memory; GB300's FP64 rate (~1 TFLOP/s) would make an FP64 read-modify-write here the
 // bottleneck.
-#include <cuda_bf16.h>
-
 #include <vector>
 
 #include "mixed.cuh"
@@ -34,7 +33,8 @@ namespace qsgw {
 
 constexpr int KBR = 16;                   // transition columns per K-block
 constexpr int KBK = 2 * KBR;              // K' per K-block (re/im pairs)
-constexpr int CHR = 512;                  // columns per exact FP32 chunk
+constexpr int CHR = 1024;                 // columns per exact FP32 chunk
+constexpr float DMAX = 90.f;              // |leading digit| bound: 2 * CHR * DMAX^2 < 2^24
 constexpr int KB_PER_CH = CHR / KBR;      // 32
 constexpr int TI = 64;                    // rows I per tile (M = 128)
 constexpr int A_PLANE = 128 * KBK * 2;    // bytes of one digit plane of one A K-block (8 KB)
@@ -46,13 +46,13 @@ constexpr int NTHREADS = 64 + NBG;
 constexpr uint32_t TMEM_L12 = 256;        // column of the level-1+2 accumulator
 constexpr uint64_t kWaitNs = 1000000000ull;
 
-// Largest e with m * 2^e <= 127 (m > 0), so that the leading digit fits in [-127, 127].
+// Largest e with m * 2^e <= DMAX (m > 0), so that the leading digit fits in [-DMAX, DMAX].
 __device__ __forceinline__ int scale_exp(float m) {
   if (!(m > 0.f) || !isfinite(m)) return 0;
   int E;
-  const float f = frexpf(m, &E);  // m = f 2^E, f in [0.5, 1)
+  const float f = frexpf(m, &E);  // m = f 2^E, f in [0.5, 1); 2^7 f <= DMAX  <=>  f <= DMAX / 128
   int e = 7 - E;
-  if (f > 127.f / 128.f) e -= 1;
+  if (f > DMAX / 128.f) e -= 1;
   return max(-120, min(120, e));
 }
 __device__ __forceinline__ float exp2i(int e) {
@@ -60,23 +60,33 @@ __device__ __forceinline__ float exp2i(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-// Three BF16-exact digits of t (|t| <= 127.5): d0 = rint(t) (integer), then the remainder split
-// twice by round-to-nearest BF16. t - d0 and u - d1 are exact in FP32 (Sterbenz).
-__device__ __forceinline__ void digits3(float t, float& d0, float& d1, float& d2) {
-  d0 = rintf(t);
-  const float u = t - d0;
-  d1 = __bfloat162float(__float2bfloat16_rn(u));
-  const float u2 = u - d1;
-  d2 = __bfloat162float(__float2bfloat16_rn(u2));
+// Rounding without the quarter-rate conversion pipe (rintf and F2F run there on this part):
+// (t + 1.5*2^23) - 1.5*2^23 is t rounded to the nearest integer (ties to even) for |t| < 2^22,
+// and a BF16 round-to-nearest-even of a finite FP32 value is an integer add and mask.
+__device__ __forceinline__ float rint_add(float t) { return (t + 12582912.0f) - 12582912.0f; }
+__device__ __forceinline__ float bf16_round(float x) {
+  uint32_t b = __float_as_uint(x);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return __uint_as_float(b & 0xFFFF0000u);
 }
 
+// Three BF16-exact digits of t (|t| <= DMAX + 1/2): d0 = rint(t) (integer), then the remainder split
+// twice by round-to-nearest BF16. t - d0 and u - d1 are exact in FP32 (Sterbenz).
+__device__ __forceinline__ void digits3(float t, float& d0, float& d1, float& d2) {
+  d0 = rint_add(t);
+  const float u = t - d0;
+  d1 = bf16_round(u);
+  const float u2 = u - d1;
+  d2 = bf16_round(u2);
+}
+
+// Two BF16-exact FP32 values -> packed bf16x2 (lo in the low half): their upper 16 bits.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
 // ------------------------------------------------------------------ prep: columns
-// One CTA per chunk of 512 columns: Delta, domain check, |w_l| in FP32 ([r][l]), and the
+// One CTA per chunk of CHR columns: Delta, domain check, |w_l| in FP32 ([r][l]), and the
 // per-chunk maximum of each |w_l| (for the B-operand scale bound).
 __global__ void __launch_bounds__(CHR) prep_cols_kernel(const double* __restrict__ eo, const double* __restrict__ eu,
                                                         int n_unocc, long long K, OmegaGrid g, float* __restrict__ wst,
@@ -312,6 +322,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           mma_bf16(tmem + TMEM_L12, a0, b2, idesc, 1u);
           mma_bf16(tmem + TMEM_L12, a2, b0, idesc, 1u);
           mma_bf16(tmem + TMEM_L12, a1, b1, idesc, 1u);
+          mma_bf16(tmem + TMEM_L12, a1, b2, idesc, 1u);
+          mma_bf16(tmem + TMEM_L12, a2, b1, idesc, 1u);
         }
         mma_commit(&empty[s]);
         mma_commit(&bempty[sb]);
@@ -328,55 +340,50 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     const int wg = (warp - 2) >> 2;           // column half handled in the epilogue
     const int m_row = quarter * 32 + lane;    // accumulator lane = A row
     const int part = m_row / TI, I = it * TI + (m_row % TI);
+    // B-operand row owned by this thread for the whole kernel (threads bt >= N only help flush)
+    const bool has_row = bt < N;
+    const int bn = has_row ? bt : 0, bl = bn / TJ, bj = bn % TJ;
+    const bool bjok = has_row && (jt * TJ + bj < p.n_pb);
+    const int boff = (bn >> 3) * 128 + (bn & 7) * 16;
+    float bsc = 0.f;
     for (int kb = 0; kb < n_kb; ++kb) {
       const int s = kb % NS, sb = kb % NSB, kbl = kb % KB_PER_CH, c = kb / KB_PER_CH;
-      if (kbl == 0) {  // B scales of this chunk: 2^eB with eB from max_r |w_l| * max_r |z_J|
-        for (int n = bt; n < N; n += NBG) {
-          const int l = n / TJ, J = jt * TJ + (n % TJ);
-          const float zm = J < p.n_pb ? p.zmax[(size_t)c * p.n_pad + J] : 0.f;
-          const int e = scale_exp(p.wmax[c * L + l] * zm);
-          sExpB[n] = e;
-          sScale[n] = exp2i(e);
-        }
+      if (kbl == 0 && has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
+        const float zm = bjok ? p.zmax[(size_t)c * p.n_pad + jt * TJ + bj] : 0.f;
+        const int e = scale_exp(p.wmax[c * L + bl] * zm);
+        sExpB[bn] = e;
+        bsc = exp2i(e);
       }
       bool ok = mbar_wait_bounded(&full[s], (kb / NS) & 1, kWaitNs);
       if (ok && kb >= NSB) ok = mbar_wait_bounded(&bempty[sb], ((kb / NSB) - 1) & 1, kWaitNs);
       // a slot per K-block parity: a thread one K-block ahead never writes the slot others still read
       if (!ok) abortB[kb & 1] = 1;
-      named_bar_sync(1, NBG);  // also orders the scale-table writes above
+      named_bar_sync(1, NBG);  // also publishes the exponent table written above
       if (abortB[kb & 1]) break;
-      const float2* raw = sRaw + s * KBR * TJ;
-      const float* ws = sW + s * KBR * L;
-      uint8_t* bdst = sB + sb * BSTAGE;
-      for (int item = bt; item < 4 * N; item += NBG) {
-        const int n = item % N, g = item / N;
-        const int l = n / TJ, j = n % TJ;
-        const bool jok = jt * TJ + j < p.n_pb;
-        const float sc = sScale[n];
-        float xr[4], xi[4];
+      if (has_row) {
+        const float2* raw = sRaw + s * KBR * TJ + bj;
+        const float* ws = sW + s * KBR * L + bl;
+        uint8_t* bdst = sB + sb * BSTAGE + boff;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          const int rl = g * 4 + rr;
-          const float2 z = jok ? raw[rl * TJ + j] : make_float2(0.f, 0.f);
-          const float ww = ws[rl * L + l] * sc;
-          xr[rr] = ww * z.x;
-          xi[rr] = ww * z.y;
-        }
-        float d[3][8];
+        for (int g = 0; g < 4; ++g) {
+          float d[3][8];
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          digits3(xr[rr], d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
-          digits3(xi[rr], d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
-        }
-        const int off = g * 16 * N + (n >> 3) * 128 + (n & 7) * 16;
+          for (int rr = 0; rr < 4; ++rr) {
+            const int rl = g * 4 + rr;
+            const float2 z = bjok ? raw[rl * TJ] : make_float2(0.f, 0.f);
+            const float ww = ws[rl * L] * bsc;
+            digits3(ww * z.x, d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
+            digits3(ww * z.y, d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
+          }
 #pragma unroll
-        for (int pl = 0; pl < 3; ++pl) {
-          uint4 v;
-          v.x = pack_bf16(d[pl][0], d[pl][1]);
-          v.y = pack_bf16(d[pl][2], d[pl][3]);
-          v.z = pack_bf16(d[pl][4], d[pl][5]);
-          v.w = pack_bf16(d[pl][6], d[pl][7]);
-          *reinterpret_cast<uint4*>(bdst + pl * BPLANE + off) = v;
+          for (int pl = 0; pl < 3; ++pl) {
+            uint4 v;
+            v.x = pack_bf16(d[pl][0], d[pl][1]);
+            v.y = pack_bf16(d[pl][2], d[pl][3]);
+            v.z = pack_bf16(d[pl][4], d[pl][5]);
+            v.w = pack_bf16(d[pl][6], d[pl][7]);
+            *reinterpret_cast<uint4*>(bdst + pl * BPLANE + g * 16 * N) = v;
+          }
         }
       }
       fence_proxy_async_smem();
@@ -394,23 +401,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         tc_fence_after();
         const int eA = p.expA[(size_t)c * p.n_pad + I];
         const bool iok = I < p.n_pb;
-        const int half = N / 2;
-        for (int col0 = wg * half; col0 < (wg + 1) * half; col0 += 8) {
-          uint32_t r0[8], r1[8];
-          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
-          tmem_ld_x8(ta, r0);
-          tmem_ld_x8(ta + TMEM_L12, r1);
+        const int half = N / 2;  // a multiple of 8
+        const size_t nn = (size_t)p.n_pad * p.n_pad;
+        float2* accI = p.acc + (size_t)part * nn + I;
+        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+        for (int col0 = wg * half; col0 < (wg + 1) * half; col0 += 16) {
+          const int cnt = min(16, (wg + 1) * half - col0);  // 16 or 8
+          uint32_t r0[16], r1[16];
+          tmem_ld_x8(tl + col0, *reinterpret_cast<uint32_t(*)[8]>(&r0[0]));
+          tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
+          if (cnt == 16) {
+            tmem_ld_x8(tl + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r0[8]));
+            tmem_ld_x8(tl + TMEM_L12 + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r1[8]));
+          }
           tmem_ld_wait();
+          // all global loads of the group first (independent), then the double-float adds and stores
+          float2 v[16];
+          size_t off[16];
+          bool okc[16];
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n % TJ);
-            if (iok && J < p.n_pb) {
-              const float sc = exp2i(-(eA + sExpB[n]));
-              float2* ap = p.acc + (((size_t)(l * 2 + part) * p.n_pad + J) * p.n_pad + I);
-              float2 v = *ap;
-              df_add(v, __uint_as_float(r0[jj]) * sc);
-              df_add(v, __uint_as_float(r1[jj]) * sc);
-              *ap = v;
+          for (int jj = 0; jj < 16; ++jj) {
+            const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
+            okc[jj] = jj < cnt && iok && J < p.n_pb;
+            off[jj] = (size_t)l * 2 * nn + (size_t)J * p.n_pad;
+            if (okc[jj]) v[jj] = accI[off[jj]];
+          }
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            if (okc[jj]) {
+              const float sc = exp2i(-(eA + sExpB[col0 + jj]));
+              df_add(v[jj], __uint_as_float(r0[jj]) * sc);
+              df_add(v[jj], __uint_as_float(r1[jj]) * sc);
+              accI[off[jj]] = v[jj];
             }
           }
         }
