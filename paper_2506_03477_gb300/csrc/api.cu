@@ -1,5 +1,5 @@
 // C ABI (include/qsgw.h): context, argument validation, host staging, stream ordering, and
-// the eps^{-1} step through cuSOLVER (FP64 Cholesky: potrf + potri).
+// the eps^{-1} step through cuSOLVER (FP64 Cholesky: potrf + potri, one stream per frequency).
 #include <cusolverDn.h>
 
 #include <cmath>
@@ -17,6 +17,16 @@ struct QAcc {
   int n_pad = 0;
   void* acc = nullptr;  // FP64: double2 [L][n_pad][n_pad]; mixed: float2 (hi, lo) planes [L][re|im][n_pad][n_pad]
   size_t bytes = 0;
+};
+
+// One cuSOLVER handle, stream and workspace per frequency, so the independent Cholesky
+// factorisations of eps(i omega_l) run concurrently (each alone leaves most SMs idle).
+struct SolverLane {
+  cudaStream_t stream = nullptr;
+  cusolverDnHandle_t handle = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaEvent_t done = nullptr;
 };
 
 struct qsgw_ctx {
@@ -37,9 +47,8 @@ struct qsgw_ctx {
   double* d_estage = nullptr;
   size_t estage_cap = 0;  // doubles
   MixedScratch mixed;
-  cusolverDnHandle_t solver = nullptr;
-  void* solver_ws = nullptr;
-  size_t solver_ws_bytes = 0;
+  SolverLane lanes[kMaxOmega];
+  cudaEvent_t fork = nullptr;
   int* d_info = nullptr;
 };
 
@@ -226,40 +235,50 @@ qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps
   const int n = a.n_pb, L = c->g.L;
   const size_t nn = (size_t)n * n;
   double2* w = static_cast<double2*>(W);
-  if (!c->solver) {
-    if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
-  }
-  if (cusolverDnSetStream(c->solver, c->stream) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
   if (!c->d_info) QSGW_CK(cudaMalloc(&c->d_info, sizeof(int) * 2 * kMaxOmega));
-  int lw1 = 0, lw2 = 0;
-  if (cusolverDnZpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, n, reinterpret_cast<cuDoubleComplex*>(w), n,
-                                  &lw1) != CUSOLVER_STATUS_SUCCESS)
-    return QSGW_ERR_CUDA;
-  if (cusolverDnZpotri_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, n, reinterpret_cast<cuDoubleComplex*>(w), n,
-                                  &lw2) != CUSOLVER_STATUS_SUCCESS)
-    return QSGW_ERR_CUDA;
-  const size_t lwork = (size_t)(lw1 > lw2 ? lw1 : lw2);
-  qsgw_status st = grow(&c->solver_ws, &c->solver_ws_bytes, sizeof(cuDoubleComplex) * (lwork + 1));
-  if (st != QSGW_OK) return st;
+  if (!c->fork) QSGW_CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+  for (int l = 0; l < L; ++l) {
+    SolverLane& ln = c->lanes[l];
+    if (!ln.stream) {
+      QSGW_CK(cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking));
+      QSGW_CK(cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming));
+      if (cusolverDnCreate(&ln.handle) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
+      if (cusolverDnSetStream(ln.handle, ln.stream) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
+    }
+    int lw1 = 0, lw2 = 0;
+    auto* m = reinterpret_cast<cuDoubleComplex*>(w + l * nn);
+    if (cusolverDnZpotrf_bufferSize(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, &lw1) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnZpotri_bufferSize(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, &lw2) != CUSOLVER_STATUS_SUCCESS)
+      return QSGW_ERR_CUDA;
+    const size_t lwork = (size_t)(lw1 > lw2 ? lw1 : lw2);
+    qsgw_status st = grow(&ln.ws, &ln.ws_bytes, sizeof(cuDoubleComplex) * (lwork + 1));
+    if (st != QSGW_OK) return st;
+  }
 
   launch_form_eps(a.acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, n, a.n_pad, L, c->spin, v, w, c->stream);
   QSGW_CK(cudaGetLastError());
   if (eps_out) QSGW_CK(cudaMemcpyAsync(eps_out, w, sizeof(double2) * nn * L, cudaMemcpyDeviceToDevice, c->stream));
-  auto* ws = static_cast<cuDoubleComplex*>(c->solver_ws);
+  QSGW_CK(cudaEventRecord(c->fork, c->stream));
   for (int l = 0; l < L; ++l) {
+    SolverLane& ln = c->lanes[l];
     auto* m = reinterpret_cast<cuDoubleComplex*>(w + l * nn);
-    if (cusolverDnZpotrf(c->solver, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, (int)lwork, c->d_info + l) !=
+    const int lwork = (int)(ln.ws_bytes / sizeof(cuDoubleComplex) - 1);
+    auto* ws = static_cast<cuDoubleComplex*>(ln.ws);
+    QSGW_CK(cudaStreamWaitEvent(ln.stream, c->fork, 0));
+    if (cusolverDnZpotrf(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, lwork, c->d_info + l) !=
         CUSOLVER_STATUS_SUCCESS)
       return QSGW_ERR_CUDA;
-    if (cusolverDnZpotri(c->solver, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, (int)lwork, c->d_info + kMaxOmega + l) !=
+    if (cusolverDnZpotri(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, lwork, c->d_info + kMaxOmega + l) !=
         CUSOLVER_STATUS_SUCCESS)
       return QSGW_ERR_CUDA;
+    QSGW_CK(cudaEventRecord(ln.done, ln.stream));
+    QSGW_CK(cudaStreamWaitEvent(c->stream, ln.done, 0));
   }
   launch_w_from_inverse(w, n, L, v, correlation_only, c->stream);
   QSGW_CK(cudaGetLastError());
   int hinfo[2 * kMaxOmega];
   QSGW_CK(cudaMemcpyAsync(hinfo, c->d_info, sizeof(int) * 2 * kMaxOmega, cudaMemcpyDeviceToHost, c->stream));
-  st = take_device_error(c);
+  qsgw_status st = take_device_error(c);
   if (st != QSGW_OK) return st;
   qsgw_status res = QSGW_OK;
   for (int l = 0; l < L; ++l) {
@@ -291,9 +310,14 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   if (c->d_zstage) cudaFree(c->d_zstage);
   if (c->d_estage) cudaFree(c->d_estage);
   mixed_free(c->mixed);
-  if (c->solver_ws) cudaFree(c->solver_ws);
+  for (auto& ln : c->lanes) {
+    if (ln.handle) cusolverDnDestroy(ln.handle);
+    if (ln.ws) cudaFree(ln.ws);
+    if (ln.done) cudaEventDestroy(ln.done);
+    if (ln.stream) cudaStreamDestroy(ln.stream);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
   if (c->d_info) cudaFree(c->d_info);
-  if (c->solver) cusolverDnDestroy(c->solver);
   if (c->d_err) cudaFree(c->d_err);
   delete c;
   return st;
