@@ -15,7 +15,7 @@ using namespace qsgw;
 struct QAcc {
   int n_pb = 0;
   int n_pad = 0;
-  void* acc = nullptr;  // FP64: double2 [L][n_pad][n_pad]; mixed: float2 (hi, lo) planes [L][re|im][n_pad][n_pad]
+  void* acc = nullptr;  // FP64: double2 [L][n_pad][n_pad]; mixed: 2 copies of float2 (hi, lo) [L][re|im][n_pad][n_pad]
   size_t bytes = 0;
 };
 
@@ -174,7 +174,8 @@ qsgw_status qsgw_chi0_init(qsgw_ctx** out, int n_q, const int* n_pb, int n_omega
     QAcc& a = c->q[i];
     a.n_pb = n_pb[i];
     a.n_pad = pad_to(n_pb[i], kPad);
-    a.bytes = (size_t)a.n_pad * a.n_pad * n_omega * (prec == QSGW_FP64 ? sizeof(double2) : sizeof(float4));
+    // mixed: two double-float copies (see herk_mixed_kernel's persistent schedule)
+    a.bytes = (size_t)a.n_pad * a.n_pad * n_omega * (prec == QSGW_FP64 ? sizeof(double2) : 2 * sizeof(float4));
     e = cudaMalloc(&a.acc, a.bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.acc, 0, a.bytes, c->stream);
     if (e != cudaSuccess) st = cuda_status(e);

@@ -60,24 +60,29 @@ __device__ __forceinline__ float exp2i(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-// Rounding without the quarter-rate conversion pipe (rintf and F2F run there on this part):
-// (t + 1.5*2^23) - 1.5*2^23 is t rounded to the nearest integer (ties to even) for |t| < 2^22,
-// and a BF16 round-to-nearest-even of a finite FP32 value is an integer add and mask.
-__device__ __forceinline__ float rint_add(float t) { return (t + 12582912.0f) - 12582912.0f; }
-__device__ __forceinline__ float bf16_round(float x) {
-  uint32_t b = __float_as_uint(x);
-  b += 0x7FFFu + ((b >> 16) & 1u);
-  return __uint_as_float(b & 0xFFFF0000u);
+// All digit arithmetic stays on the full-rate FP32 pipe (rintf and F2F use the quarter-rate
+// conversion pipe on this part, integer rounding the half-rate ALU pipe). The _rn intrinsics are
+// never contracted into FMAs, which both tricks below rely on.
+// (t + 1.5*2^23) - 1.5*2^23 is t rounded to the nearest integer (ties to even) for |t| < 2^22.
+__device__ __forceinline__ float rint_add(float t) {
+  return __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
+}
+// Veltkamp splitting with factor 2^16 + 1: hi = c - (c - x), c = (2^16 + 1) x, keeps the leading
+// 24 - 16 = 8 significant bits of x (round to nearest), so hi is exactly representable in BF16
+// (same exponent range as FP32) and x - hi is exact.
+__device__ __forceinline__ float split_bf16(float x) {
+  const float c = __fmul_rn(65537.0f, x);
+  return __fsub_rn(c, __fsub_rn(c, x));
 }
 
 // Three BF16-exact digits of t (|t| <= DMAX + 1/2): d0 = rint(t) (integer), then the remainder split
-// twice by round-to-nearest BF16. t - d0 and u - d1 are exact in FP32 (Sterbenz).
+// twice into leading 8-bit parts. t - d0 and u - d1 are exact in FP32 (Sterbenz).
 __device__ __forceinline__ void digits3(float t, float& d0, float& d1, float& d2) {
   d0 = rint_add(t);
-  const float u = t - d0;
-  d1 = bf16_round(u);
-  const float u2 = u - d1;
-  d2 = bf16_round(u2);
+  const float u = __fsub_rn(t, d0);
+  d1 = split_bf16(u);
+  const float u2 = __fsub_rn(u, d1);
+  d2 = split_bf16(u2);
 }
 
 // Two BF16-exact FP32 values -> packed bf16x2 (lo in the low half): their upper 16 bits.
@@ -196,8 +201,9 @@ struct MainArgs {
   const int* expA;
   const float* wmax;
   const int2* tiles;
-  float2* acc;  // [l][part][J][I] (hi, lo)
-  int n_pb, n_pad, L, TJ, N, n_kb, n_jt;
+  float2* acc;   // [l][part][J][I] (hi, lo): chunks of a tile processed by the tile's first CTA
+  float2* acc2;  // same layout: chunks of a tile whose first chunk belongs to the previous CTA
+  int n_pb, n_pad, L, TJ, N, n_kb, n_jt, n_tiles, n_ch;
   uint32_t idesc;
   int* d_err;
 };
@@ -236,8 +242,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint64_t* accempty = accfull + 1;  // 8 epilogue warps -> MMA
   uint64_t* finbar = accempty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(finbar + 1);
-  int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [3]: B-gen K-block slots (parity) + epilogue
-  int* abortP = abortB + 3;
+  int* abortP = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -252,7 +257,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     mbar_init(accfull, 1);
     mbar_init(accempty, NBG / 32);
     mbar_init(finbar, 1);
-    abortB[0] = abortB[1] = abortB[2] = 0;
     *abortP = 0;
     fence_mbar_init();
   }
@@ -264,41 +268,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int2 tile = p.tiles[blockIdx.x];
-  const int it = tile.x, jt = tile.y;
-  const int n_kb = p.n_kb;
+  // Persistent schedule: the (tile, chunk) items, tile-major, are split into gridDim.x contiguous
+  // ranges of equal length (each >= one tile's chunks, so a tile spans at most two CTAs).
+  // g counts this CTA's K-blocks; item = beg + g / KB_PER_CH.
+  const int C = p.n_ch;
+  const long long total = (long long)p.n_tiles * C;
+  const long long beg = total * blockIdx.x / gridDim.x, end = total * (blockIdx.x + 1) / gridDim.x;
+  const int n_g = (int)(end - beg) * KB_PER_CH;
 
   if (warp == 0) {
     // ---------------- producer: bulk copies of the A digit planes, raw B values and weights
     if (lane == 0) {
       const uint32_t raw_bytes = KBR * TJ * 8, w_bytes = KBR * L * 4;
       int issued = 0;
-      for (int kb = 0; kb < n_kb; ++kb) {
-        const int s = kb % NS, round = kb / NS;
-        if (kb >= NS && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitNs)) {
+      for (int g = 0; g < n_g; ++g) {
+        const int s = g % NS, round = g / NS;
+        const long long item = beg + g / KB_PER_CH;
+        const int2 tile = p.tiles[item / C];
+        const int kb = (int)(item % C) * KB_PER_CH + g % KB_PER_CH;
+        if (g >= NS && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitNs)) {
           *abortP = 1;
           atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
           break;
         }
         mbar_arrive_expect_tx(&full[s], A_STAGE + raw_bytes + w_bytes);
-        bulk_g2s(sA + s * A_STAGE, p.aplanes + ((size_t)it * n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
-        bulk_g2s(sRaw + s * KBR * TJ, p.braw + ((size_t)jt * n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
+        bulk_g2s(sA + s * A_STAGE, p.aplanes + ((size_t)tile.x * p.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
+        bulk_g2s(sRaw + s * KBR * TJ, p.braw + ((size_t)tile.y * p.n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
         bulk_g2s(sW + s * KBR * L, p.wst + (size_t)kb * KBR * L, w_bytes, &full[s]);
-        issued = kb + 1;
+        issued = g + 1;
       }
       // never leave a bulk copy in flight into shared memory at exit
-      for (int kb = (issued > NS ? issued - NS : 0); kb < issued; ++kb)
-        mbar_wait_bounded(&full[kb % NS], (kb / NS) & 1, kWaitNs);
+      for (int g = (issued > NS ? issued - NS : 0); g < issued; ++g)
+        mbar_wait_bounded(&full[g % NS], (g / NS) & 1, kWaitNs);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
       const uint32_t idesc = p.idesc;
-      for (int kb = 0; kb < n_kb; ++kb) {
-        const int s = kb % NS, sb = kb % NSB, kbl = kb % KB_PER_CH;
-        bool ok = mbar_wait_bounded(&full[s], (kb / NS) & 1, kWaitNs);
-        ok = ok && mbar_wait_bounded(&bfull[sb], (kb / NSB) & 1, kWaitNs);
-        if (ok && kbl == 0 && kb > 0) ok = mbar_wait_bounded(accempty, ((kb / KB_PER_CH) - 1) & 1, kWaitNs);
+      for (int g = 0; g < n_g; ++g) {
+        const int s = g % NS, sb = g % NSB, kbl = g % KB_PER_CH;
+        bool ok = mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
+        ok = ok && mbar_wait_bounded(&bfull[sb], (g / NSB) & 1, kWaitNs);
+        if (ok && kbl == 0 && g > 0) ok = mbar_wait_bounded(accempty, ((g / KB_PER_CH) - 1) & 1, kWaitNs);
         if (!ok) {
           *abortP = 1;
           atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
@@ -339,28 +350,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
     const int wg = (warp - 2) >> 2;           // column half handled in the epilogue
     const int m_row = quarter * 32 + lane;    // accumulator lane = A row
-    const int part = m_row / TI, I = it * TI + (m_row % TI);
+    const int part = m_row / TI;
     // B-operand row owned by this thread for the whole kernel (threads bt >= N only help flush)
     const bool has_row = bt < N;
     const int bn = has_row ? bt : 0, bl = bn / TJ, bj = bn % TJ;
-    const bool bjok = has_row && (jt * TJ + bj < p.n_pb);
     const int boff = (bn >> 3) * 128 + (bn & 7) * 16;
     float bsc = 0.f;
-    for (int kb = 0; kb < n_kb; ++kb) {
-      const int s = kb % NS, sb = kb % NSB, kbl = kb % KB_PER_CH, c = kb / KB_PER_CH;
-      if (kbl == 0 && has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
-        const float zm = bjok ? p.zmax[(size_t)c * p.n_pad + jt * TJ + bj] : 0.f;
-        const int e = scale_exp(p.wmax[c * L + bl] * zm);
-        sExpB[bn] = e;
-        bsc = exp2i(e);
+    bool bjok = false;
+    int it = 0, jt = 0, c = 0;
+    bool second = false;
+    // A warp whose wait timed out keeps iterating without waits or work ("dead"), so every named
+    // barrier below is still reached by all builder threads; dead is warp-uniform, as the
+    // warp-collective TMEM loads require.
+    bool dead = false;
+    for (int g = 0; g < n_g; ++g) {
+      const int s = g % NS, sb = g % NSB, kbl = g % KB_PER_CH, lc = g / KB_PER_CH;
+      if (kbl == 0) {  // new (tile, chunk) item
+        const long long item = beg + lc;
+        const int t = (int)(item / C);
+        const int2 tile = p.tiles[t];
+        it = tile.x;
+        jt = tile.y;
+        c = (int)(item % C);
+        second = (long long)t * C < beg;
+        bjok = has_row && (jt * TJ + bj < p.n_pb);
+        if (has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
+          const float zm = bjok ? p.zmax[(size_t)c * p.n_pad + jt * TJ + bj] : 0.f;
+          const int e = scale_exp(p.wmax[c * L + bl] * zm);
+          sExpB[bn] = e;
+          bsc = exp2i(e);
+        }
       }
-      bool ok = mbar_wait_bounded(&full[s], (kb / NS) & 1, kWaitNs);
-      if (ok && kb >= NSB) ok = mbar_wait_bounded(&bempty[sb], ((kb / NSB) - 1) & 1, kWaitNs);
-      // a slot per K-block parity: a thread one K-block ahead never writes the slot others still read
-      if (!ok) abortB[kb & 1] = 1;
-      named_bar_sync(1, NBG);  // also publishes the exponent table written above
-      if (abortB[kb & 1]) break;
-      if (has_row) {
+      bool ok = !dead && mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
+      if (ok && g >= NSB) ok = mbar_wait_bounded(&bempty[sb], ((g / NSB) - 1) & 1, kWaitNs);
+      if (!dead && __any_sync(0xffffffffu, !ok)) {
+        dead = true;
+        atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+      }
+      if (has_row && !dead) {
         const float2* raw = sRaw + s * KBR * TJ + bj;
         const float* ws = sW + s * KBR * L + bl;
         uint8_t* bdst = sB + sb * BSTAGE + boff;
@@ -388,25 +415,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) {
+      if (lane == 0 && !dead) {
         mbar_arrive(&bfull[sb]);
         mbar_arrive(&empty[s]);
       }
       if (kbl == KB_PER_CH - 1) {
         // ------------- chunk epilogue: TMEM -> registers -> scaled -> double-float global accumulator
-        ok = mbar_wait_bounded(accfull, c & 1, kWaitNs);
-        if (!ok) abortB[2] = 1;
-        named_bar_sync(1, NBG);
-        if (abortB[2]) break;
+        ok = !dead && mbar_wait_bounded(accfull, lc & 1, kWaitNs);
+        if (!dead && __any_sync(0xffffffffu, !ok)) {
+          dead = true;
+          atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+        }
+        named_bar_sync(1, NBG);  // the chunk's exponent table (written at chunk start) is complete
         tc_fence_after();
+        const int I = it * TI + (m_row % TI);
         const int eA = p.expA[(size_t)c * p.n_pad + I];
         const bool iok = I < p.n_pb;
         const int half = N / 2;  // a multiple of 8
         const size_t nn = (size_t)p.n_pad * p.n_pad;
-        float2* accI = p.acc + (size_t)part * nn + I;
+        float2* accI = (second ? p.acc2 : p.acc) + (size_t)part * nn + I;
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        for (int col0 = wg * half; col0 < (wg + 1) * half; col0 += 16) {
-          const int cnt = min(16, (wg + 1) * half - col0);  // 16 or 8
+        const int col_end = dead ? wg * half : (wg + 1) * half;  // a dead warp skips the flush
+        for (int col0 = wg * half; col0 < col_end; col0 += 16) {
+          const int cnt = min(16, col_end - col0);  // 16 or 8
           uint32_t r0[16], r1[16];
           tmem_ld_x8(tl + col0, *reinterpret_cast<uint32_t(*)[8]>(&r0[0]));
           tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
@@ -438,8 +469,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(accempty);
-        named_bar_sync(1, NBG);  // scale table of this chunk no longer needed
+        if (lane == 0 && !dead) mbar_arrive(accempty);
+        named_bar_sync(1, NBG);  // exponent table of this chunk no longer needed
       }
     }
   }
@@ -522,6 +553,7 @@ qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, i
   a.wmax = wmax;
   a.tiles = static_cast<const int2*>(s.aux);
   a.acc = reinterpret_cast<float2*>(acc);
+  a.acc2 = a.acc + (size_t)L * 2 * n_pad * n_pad;
   a.n_pb = n_pb;
   a.n_pad = n_pad;
   a.L = L;
@@ -529,6 +561,8 @@ qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, i
   a.N = N;
   a.n_kb = n_kb;
   a.n_jt = n_jt;
+  a.n_tiles = s.n_tiles;
+  a.n_ch = n_ch;
   a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
   a.d_err = d_err;
   const size_t smem = main_smem_bytes(N, TJ, L);
@@ -538,7 +572,15 @@ qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, i
       return QSGW_ERR_CUDA;
     s.attr_set = true;
   }
-  herk_mixed_kernel<<<s.n_tiles, NTHREADS, smem, stream>>>(a);
+  if (s.n_sm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return QSGW_ERR_CUDA;
+  }
+  // one persistent CTA per SM (fewer if there are fewer tiles, so every CTA covers >= one tile)
+  const int grid = s.n_tiles < s.n_sm ? s.n_tiles : s.n_sm;
+  herk_mixed_kernel<<<grid, NTHREADS, smem, stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
 }
 

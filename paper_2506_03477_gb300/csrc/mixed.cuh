@@ -15,9 +15,11 @@ struct MixedScratch {
   int tiles_key_n = -1;
   int tiles_key_tj = -1;
   bool attr_set = false;
+  int n_sm = 0;
 };
 
-// acc: double-float accumulator, float2 (hi, lo) planes [L][2 (re, im)][n_pad (J)][n_pad (I)].
+// acc: two double-float accumulators back to back, each float2 (hi, lo) planes
+// [L][2 (re, im)][n_pad (J)][n_pad (I)]; chi0 is their sum.
 qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, int n_pb, int n_pad, int n_occ,
                              int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
                              int* d_err, cudaStream_t stream);
