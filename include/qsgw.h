@@ -87,6 +87,26 @@ qsgw_status qsgw_chi0_init(qsgw_ctx **ctx, int n_q, const int *n_pb, int n_omega
 qsgw_status qsgw_chi0_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_unocc,
                                  const double *eps_occ, const double *eps_unocc, int n_omega, const double *omega);
 
+/* One block of transition columns (normally one k-point) for one q-point; see
+ * qsgw_chi0_accumulate for the meaning and layout of every field. All pointers device. */
+typedef struct {
+  int q;
+  const void *Z;
+  long long ldz;
+  int n_occ, n_unocc;
+  const double *eps_occ;
+  const double *eps_unocc;
+} qsgw_block;
+
+/* Batched form of qsgw_chi0_accumulate over independent q-points (Alg. 1 loops over q). The
+ * blocks must name distinct q (QSGW_ERR_ARG otherwise), at most 32 per call, all pointers on the
+ * device. In QSGW_MIXED_BF16X3 every block's operands are prepared and then ONE persistent
+ * tensor-core launch works through all (block, tile, chunk) items, balanced over the SMs, so
+ * uneven n_pb and column counts share the GPU; in QSGW_FP64 the blocks run one after another.
+ * The first call with a new set of shapes allocates scratch and tile lists; after such a warm-up
+ * call the sequence contains only kernel launches and can be captured in a CUDA graph. */
+qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx *ctx, int n_blocks, const qsgw_block *blocks);
+
 /* Write chi0(q) (the scaled, mirrored accumulator: full Hermitian, imaginary part of the
  * diagonal exactly zero) into chi0, device complex128 [n_omega][n_pb][n_pb]. Synchronises
  * the stream and returns any sticky device error. The accumulator is kept. */

@@ -220,6 +220,35 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ld
   return accumulate_device(c, q, Zd, ldz, n_occ, n_unocc, eo, eu);
 }
 
+qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
+  if (!c || n_blocks < 1 || n_blocks > 32 || !blocks) return QSGW_ERR_ARG;
+  MixedBlock mb[32];
+  for (int i = 0; i < n_blocks; ++i) {
+    const qsgw_block& b = blocks[i];
+    if (b.q < 0 || b.q >= c->n_q || !b.Z || !b.eps_occ || !b.eps_unocc || b.n_occ < 1 || b.n_unocc < 1)
+      return QSGW_ERR_ARG;
+    const QAcc& a = c->q[b.q];
+    if (b.ldz < a.n_pb || (long long)b.n_occ * b.n_unocc > (1LL << 31)) return QSGW_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (blocks[j].q == b.q) return QSGW_ERR_ARG;
+    if (!is_device_ptr(b.Z) || !is_device_ptr(b.eps_occ) || !is_device_ptr(b.eps_unocc)) return QSGW_ERR_ARG;
+    mb[i] = MixedBlock{static_cast<const double2*>(b.Z), b.ldz, a.n_pb, a.n_pad, b.n_occ, b.n_unocc, b.eps_occ,
+                       b.eps_unocc, static_cast<float4*>(a.acc)};
+  }
+  if (c->prec == QSGW_FP64) {
+    for (int i = 0; i < n_blocks; ++i) {
+      const qsgw_block& b = blocks[i];
+      qsgw_status st = accumulate_device(c, b.q, static_cast<const double2*>(b.Z), b.ldz, b.n_occ, b.n_unocc,
+                                         b.eps_occ, b.eps_unocc);
+      if (st != QSGW_OK) return st;
+    }
+    return QSGW_OK;
+  }
+  qsgw_status st = mixed_accumulate_batch(c->mixed, n_blocks, mb, c->g, c->d_err, c->stream);
+  if (st != QSGW_OK) return st;
+  return cuda_status(cudaGetLastError());
+}
+
 qsgw_status qsgw_chi0_finalize(qsgw_ctx* c, int q, void* chi0) {
   if (!c || q < 0 || q >= c->n_q || !chi0) return QSGW_ERR_ARG;
   const QAcc& a = c->q[q];

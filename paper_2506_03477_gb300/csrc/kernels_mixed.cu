@@ -24,6 +24,7 @@
 // are scaled by 2^-(eA+eB) (exact) and added into a double-float (2 x FP32) accumulator in
 // global memory; GB300's FP64 rate (~1 TFLOP/s) would make an FP64 read-modify-write here the
 // bottleneck.
+#include <cstring>
 #include <vector>
 
 #include "mixed.cuh"
@@ -193,7 +194,8 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const double2* __restric
 }
 
 // ------------------------------------------------------------------ main tensor-core kernel
-struct MainArgs {
+// One block of transition columns (one accumulate request) for one q-point, as the kernel sees it.
+struct BlockDesc {
   const uint8_t* aplanes;
   const float2* braw;
   const float* wst;
@@ -203,10 +205,25 @@ struct MainArgs {
   const int2* tiles;
   float2* acc;   // [l][part][J][I] (hi, lo): chunks of a tile processed by the tile's first CTA
   float2* acc2;  // same layout: chunks of a tile whose first chunk belongs to the previous CTA
-  int n_pb, n_pad, L, TJ, N, n_kb, n_jt, n_tiles, n_ch;
+  long long item_off;  // first (tile, chunk) item of this block in the launch's item list
+  int n_pb, n_pad, n_kb, n_tiles, n_ch;
+};
+constexpr int kMaxBlocks = 32;  // blocks per launch (descriptors travel by value as kernel parameters)
+
+struct MainArgs {
+  BlockDesc blk[kMaxBlocks];
+  int nb;
+  long long total_items;
+  int L, TJ, N;
   uint32_t idesc;
   int* d_err;
 };
+
+// Block that holds `item`, searching forward from `b` (items are visited in increasing order).
+__device__ __forceinline__ int block_of(const BlockDesc* blk, int nb, int b, long long item) {
+  while (b + 1 < nb && blk[b + 1].item_off <= item) ++b;
+  return b;
+}
 
 __device__ __forceinline__ void df_add(float2& v, float x) {
   const float s = v.x + x;
@@ -218,7 +235,7 @@ __device__ __forceinline__ void df_add(float2& v, float x) {
 
 __host__ __device__ constexpr size_t main_smem_bytes(int N, int TJ, int L) {
   return 1024 + (size_t)NS * A_STAGE + (size_t)NSB * 3 * 64 * N + (size_t)NS * KBR * TJ * 8 +
-         (size_t)NS * KBR * L * 4 + 256 * 4 * 2 + 32 * 8 + 64;
+         (size_t)NS * KBR * L * 4 + 256 * 4 * 2 + 32 * 8 + 64 + sizeof(BlockDesc) * kMaxBlocks;
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
@@ -243,6 +260,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint64_t* finbar = accempty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(finbar + 1);
   int* abortP = reinterpret_cast<int*>(tmem_slot + 1);
+  BlockDesc* sBlk = reinterpret_cast<BlockDesc*>(bars + 32);  // block table, copied from the parameters
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -264,37 +282,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
+  for (int i = tid; i < p.nb; i += NTHREADS) sBlk[i] = p.blk[i];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // Persistent schedule: the (tile, chunk) items, tile-major, are split into gridDim.x contiguous
-  // ranges of equal length (each >= one tile's chunks, so a tile spans at most two CTAs).
-  // g counts this CTA's K-blocks; item = beg + g / KB_PER_CH.
-  const int C = p.n_ch;
-  const long long total = (long long)p.n_tiles * C;
+  // Persistent schedule: the (block, tile, chunk) items, block- then tile-major, are split into
+  // gridDim.x contiguous ranges of equal length (each >= one tile's chunks of any block, so a tile
+  // spans at most two CTAs). g counts this CTA's K-blocks; item = beg + g / KB_PER_CH.
+  const long long total = p.total_items;
   const long long beg = total * blockIdx.x / gridDim.x, end = total * (blockIdx.x + 1) / gridDim.x;
   const int n_g = (int)(end - beg) * KB_PER_CH;
+  const int nb = p.nb;
 
   if (warp == 0) {
     // ---------------- producer: bulk copies of the A digit planes, raw B values and weights
     if (lane == 0) {
       const uint32_t raw_bytes = KBR * TJ * 8, w_bytes = KBR * L * 4;
-      int issued = 0;
+      int issued = 0, b = 0;
       for (int g = 0; g < n_g; ++g) {
         const int s = g % NS, round = g / NS;
         const long long item = beg + g / KB_PER_CH;
-        const int2 tile = p.tiles[item / C];
-        const int kb = (int)(item % C) * KB_PER_CH + g % KB_PER_CH;
+        b = block_of(sBlk, nb, b, item);
+        const BlockDesc& bd = sBlk[b];
+        const long long li = item - bd.item_off;
+        const int2 tile = bd.tiles[li / bd.n_ch];
+        const int kb = (int)(li % bd.n_ch) * KB_PER_CH + g % KB_PER_CH;
         if (g >= NS && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitNs)) {
           *abortP = 1;
           atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
           break;
         }
         mbar_arrive_expect_tx(&full[s], A_STAGE + raw_bytes + w_bytes);
-        bulk_g2s(sA + s * A_STAGE, p.aplanes + ((size_t)tile.x * p.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
-        bulk_g2s(sRaw + s * KBR * TJ, p.braw + ((size_t)tile.y * p.n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
-        bulk_g2s(sW + s * KBR * L, p.wst + (size_t)kb * KBR * L, w_bytes, &full[s]);
+        bulk_g2s(sA + s * A_STAGE, bd.aplanes + ((size_t)tile.x * bd.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
+        bulk_g2s(sRaw + s * KBR * TJ, bd.braw + ((size_t)tile.y * bd.n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
+        bulk_g2s(sW + s * KBR * L, bd.wst + (size_t)kb * KBR * L, w_bytes, &full[s]);
         issued = g + 1;
       }
       // never leave a bulk copy in flight into shared memory at exit
@@ -357,7 +379,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     const int boff = (bn >> 3) * 128 + (bn & 7) * 16;
     float bsc = 0.f;
     bool bjok = false;
-    int it = 0, jt = 0, c = 0;
+    int it = 0, jt = 0, c = 0, b = 0;
     bool second = false;
     // A warp whose wait timed out keeps iterating without waits or work ("dead"), so every named
     // barrier below is still reached by all builder threads; dead is warp-uniform, as the
@@ -365,18 +387,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     bool dead = false;
     for (int g = 0; g < n_g; ++g) {
       const int s = g % NS, sb = g % NSB, kbl = g % KB_PER_CH, lc = g / KB_PER_CH;
-      if (kbl == 0) {  // new (tile, chunk) item
+      if (kbl == 0) {  // new (block, tile, chunk) item
         const long long item = beg + lc;
-        const int t = (int)(item / C);
-        const int2 tile = p.tiles[t];
+        b = block_of(sBlk, nb, b, item);
+        const BlockDesc& bd = sBlk[b];
+        const long long li = item - bd.item_off;
+        const int t = (int)(li / bd.n_ch);
+        const int2 tile = bd.tiles[t];
         it = tile.x;
         jt = tile.y;
-        c = (int)(item % C);
-        second = (long long)t * C < beg;
-        bjok = has_row && (jt * TJ + bj < p.n_pb);
+        c = (int)(li % bd.n_ch);
+        second = bd.item_off + (long long)t * bd.n_ch < beg;
+        bjok = has_row && (jt * TJ + bj < bd.n_pb);
         if (has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
-          const float zm = bjok ? p.zmax[(size_t)c * p.n_pad + jt * TJ + bj] : 0.f;
-          const int e = scale_exp(p.wmax[c * L + bl] * zm);
+          const float zm = bjok ? bd.zmax[(size_t)c * bd.n_pad + jt * TJ + bj] : 0.f;
+          const int e = scale_exp(bd.wmax[c * L + bl] * zm);
           sExpB[bn] = e;
           bsc = exp2i(e);
         }
@@ -392,11 +417,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         const float* ws = sW + s * KBR * L + bl;
         uint8_t* bdst = sB + sb * BSTAGE + boff;
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
+        for (int kg = 0; kg < 4; ++kg) {
           float d[3][8];
 #pragma unroll
           for (int rr = 0; rr < 4; ++rr) {
-            const int rl = g * 4 + rr;
+            const int rl = kg * 4 + rr;
             const float2 z = bjok ? raw[rl * TJ] : make_float2(0.f, 0.f);
             const float ww = ws[rl * L] * bsc;
             digits3(ww * z.x, d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
@@ -409,7 +434,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             v.y = pack_bf16(d[pl][2], d[pl][3]);
             v.z = pack_bf16(d[pl][4], d[pl][5]);
             v.w = pack_bf16(d[pl][6], d[pl][7]);
-            *reinterpret_cast<uint4*>(bdst + pl * BPLANE + g * 16 * N) = v;
+            *reinterpret_cast<uint4*>(bdst + pl * BPLANE + kg * 16 * N) = v;
           }
         }
       }
@@ -428,12 +453,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         }
         named_bar_sync(1, NBG);  // the chunk's exponent table (written at chunk start) is complete
         tc_fence_after();
+        const BlockDesc& bd = sBlk[b];
         const int I = it * TI + (m_row % TI);
-        const int eA = p.expA[(size_t)c * p.n_pad + I];
-        const bool iok = I < p.n_pb;
+        const int eA = bd.expA[(size_t)c * bd.n_pad + I];
+        const bool iok = I < bd.n_pb;
         const int half = N / 2;  // a multiple of 8
-        const size_t nn = (size_t)p.n_pad * p.n_pad;
-        float2* accI = (second ? p.acc2 : p.acc) + (size_t)part * nn + I;
+        const size_t nn = (size_t)bd.n_pad * bd.n_pad;
+        float2* accI = (second ? bd.acc2 : bd.acc) + (size_t)part * nn + I;
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         const int col_end = dead ? wg * half : (wg + 1) * half;  // a dead warp skips the flush
         for (int col0 = wg * half; col0 < col_end; col0 += 16) {
@@ -453,8 +479,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
-            okc[jj] = jj < cnt && iok && J < p.n_pb;
-            off[jj] = (size_t)l * 2 * nn + (size_t)J * p.n_pad;
+            okc[jj] = jj < cnt && iok && J < bd.n_pb;
+            off[jj] = (size_t)l * 2 * nn + (size_t)J * bd.n_pad;
             if (okc[jj]) v[jj] = accI[off[jj]];
           }
 #pragma unroll
@@ -493,24 +519,63 @@ static int tile_width(int L) {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, int n_pb, int n_pad, int n_occ,
-                             int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
-                             int* d_err, cudaStream_t stream) {
-  const int L = g.L, TJ = tile_width(L), N = TJ * L;
-  if (TJ < 1 || N < 16 || N > 256) return QSGW_ERR_ARG;
-  const long long K = (long long)n_occ * n_unocc;
-  const int n_ch = (int)((K + CHR - 1) / CHR), n_kb = n_ch * KB_PER_CH;
+// Device list of the tiles on or above the diagonal for one (n_pb, TJ), cached in the scratch.
+static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, const int2** out, int* count) {
+  for (auto& e : s.tile_lists)
+    if (e.n_pb == n_pb && e.tj == TJ) {
+      *out = e.tiles;
+      *count = e.count;
+      return QSGW_OK;
+    }
+  std::vector<int2> tl;
   const int n_it = n_pad / TI, n_jt = (n_pb + TJ - 1) / TJ;
+  for (int it = 0; it < n_it; ++it)
+    for (int jt = 0; jt < n_jt; ++jt)
+      if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) tl.push_back(make_int2(it, jt));
+  int2* d = nullptr;
+  if (cudaMalloc(&d, tl.size() * sizeof(int2)) != cudaSuccess) return QSGW_ERR_NOMEM;
+  if (cudaMemcpy(d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return QSGW_ERR_CUDA;
+  }
+  s.tile_lists.push_back({n_pb, TJ, (int)tl.size(), d});
+  *out = d;
+  *count = (int)tl.size();
+  return QSGW_OK;
+}
 
-  const size_t sz_a = (size_t)n_it * n_kb * A_STAGE;
-  const size_t sz_raw = (size_t)n_jt * n_kb * KBR * TJ * sizeof(float2);
-  const size_t sz_w = (size_t)n_kb * KBR * L * sizeof(float);
-  const size_t sz_zmax = (size_t)n_ch * n_pad * sizeof(float);
-  const size_t sz_exp = (size_t)n_ch * n_pad * sizeof(int);
-  const size_t sz_wmax = (size_t)n_ch * L * sizeof(float);
-  const size_t o_raw = align256(sz_a), o_w = o_raw + align256(sz_raw), o_zmax = o_w + align256(sz_w);
-  const size_t o_exp = o_zmax + align256(sz_zmax), o_wmax = o_exp + align256(sz_exp);
-  const size_t total = o_wmax + align256(sz_wmax);
+qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in, const OmegaGrid& g, int* d_err,
+                                   cudaStream_t stream) {
+  const int L = g.L, TJ = tile_width(L), N = TJ * L;
+  if (TJ < 1 || N < 16 || N > 256 || nb < 1 || nb > kMaxBlocks) return QSGW_ERR_ARG;
+  struct Plan {
+    long long K;
+    int n_ch, n_kb, n_it, n_jt;
+    size_t o_a, o_raw, o_w, o_zmax, o_exp, o_wmax;
+  };
+  std::vector<Plan> pl(nb);
+  size_t total = 0;
+  for (int b = 0; b < nb; ++b) {
+    Plan& P = pl[b];
+    const MixedBlock& B = in[b];
+    P.K = (long long)B.n_occ * B.n_unocc;
+    P.n_ch = (int)((P.K + CHR - 1) / CHR);
+    P.n_kb = P.n_ch * KB_PER_CH;
+    P.n_it = B.n_pad / TI;
+    P.n_jt = (B.n_pb + TJ - 1) / TJ;
+    P.o_a = total;
+    total += align256((size_t)P.n_it * P.n_kb * A_STAGE);
+    P.o_raw = total;
+    total += align256((size_t)P.n_jt * P.n_kb * KBR * TJ * sizeof(float2));
+    P.o_w = total;
+    total += align256((size_t)P.n_kb * KBR * L * sizeof(float));
+    P.o_zmax = total;
+    total += align256((size_t)P.n_ch * B.n_pad * sizeof(float));
+    P.o_exp = total;
+    total += align256((size_t)P.n_ch * B.n_pad * sizeof(int));
+    P.o_wmax = total;
+    total += align256((size_t)P.n_ch * L * sizeof(float));
+  }
   if (s.planes_cap < total) {
     if (s.planes) cudaFree(s.planes);
     s.planes = nullptr;
@@ -518,75 +583,78 @@ qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, i
     if (cudaMalloc(&s.planes, total) != cudaSuccess) return QSGW_ERR_NOMEM;
     s.planes_cap = total;
   }
-  // tile list (upper triangle: some J >= some I), rebuilt when the shape changes
-  if (s.tiles_key_n != n_pb || s.tiles_key_tj != TJ) {
-    std::vector<int2> tl;
-    for (int it = 0; it < n_it; ++it)
-      for (int jt = 0; jt < n_jt; ++jt)
-        if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) tl.push_back(make_int2(it, jt));
-    if (s.aux) cudaFree(s.aux);
-    s.aux = nullptr;
-    if (cudaMalloc(&s.aux, tl.size() * sizeof(int2)) != cudaSuccess) return QSGW_ERR_NOMEM;
-    if (cudaMemcpy(s.aux, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
-      return QSGW_ERR_CUDA;
-    s.n_tiles = (int)tl.size();
-    s.tiles_key_n = n_pb;
-    s.tiles_key_tj = TJ;
-  }
-  uint8_t* base = static_cast<uint8_t*>(s.planes);
-  auto* aplanes = base;
-  auto* braw = reinterpret_cast<float2*>(base + o_raw);
-  auto* wst = reinterpret_cast<float*>(base + o_w);
-  auto* zmax = reinterpret_cast<float*>(base + o_zmax);
-  auto* expA = reinterpret_cast<int*>(base + o_exp);
-  auto* wmax = reinterpret_cast<float*>(base + o_wmax);
-
-  prep_cols_kernel<<<n_ch, CHR, 0, stream>>>(eo, eu, n_unocc, K, g, wst, wmax, d_err);
-  prep_rows_kernel<<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt, aplanes, braw,
-                                                          zmax, expA);
-  MainArgs a;
-  a.aplanes = aplanes;
-  a.braw = braw;
-  a.wst = wst;
-  a.zmax = zmax;
-  a.expA = expA;
-  a.wmax = wmax;
-  a.tiles = static_cast<const int2*>(s.aux);
-  a.acc = reinterpret_cast<float2*>(acc);
-  a.acc2 = a.acc + (size_t)L * 2 * n_pad * n_pad;
-  a.n_pb = n_pb;
-  a.n_pad = n_pad;
-  a.L = L;
-  a.TJ = TJ;
-  a.N = N;
-  a.n_kb = n_kb;
-  a.n_jt = n_jt;
-  a.n_tiles = s.n_tiles;
-  a.n_ch = n_ch;
-  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
-  a.d_err = d_err;
-  const size_t smem = main_smem_bytes(N, TJ, L);
-  if (!s.attr_set) {
-    if (cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-        cudaSuccess)
-      return QSGW_ERR_CUDA;
-    s.attr_set = true;
-  }
   if (s.n_sm == 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&s.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return QSGW_ERR_CUDA;
   }
-  // one persistent CTA per SM (fewer if there are fewer tiles, so every CTA covers >= one tile)
-  const int grid = s.n_tiles < s.n_sm ? s.n_tiles : s.n_sm;
-  herk_mixed_kernel<<<grid, NTHREADS, smem, stream>>>(a);
+  if (!s.attr_set) {
+    if (cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+        cudaSuccess)
+      return QSGW_ERR_CUDA;
+    s.attr_set = true;
+  }
+  MainArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nb = nb;
+  a.L = L;
+  a.TJ = TJ;
+  a.N = N;
+  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
+  a.d_err = d_err;
+  uint8_t* base = static_cast<uint8_t*>(s.planes);
+  long long items = 0;
+  int max_ch = 1, min_tiles = 1 << 30;
+  for (int b = 0; b < nb; ++b) {
+    const Plan& P = pl[b];
+    const MixedBlock& B = in[b];
+    BlockDesc& d = a.blk[b];
+    qsgw_status st = tile_list(s, B.n_pb, B.n_pad, TJ, &d.tiles, &d.n_tiles);
+    if (st != QSGW_OK) return st;
+    d.aplanes = base + P.o_a;
+    d.braw = reinterpret_cast<float2*>(base + P.o_raw);
+    d.wst = reinterpret_cast<float*>(base + P.o_w);
+    d.zmax = reinterpret_cast<float*>(base + P.o_zmax);
+    d.expA = reinterpret_cast<int*>(base + P.o_exp);
+    d.wmax = reinterpret_cast<float*>(base + P.o_wmax);
+    d.acc = reinterpret_cast<float2*>(B.acc);
+    d.acc2 = d.acc + (size_t)L * 2 * B.n_pad * B.n_pad;
+    d.item_off = items;
+    d.n_pb = B.n_pb;
+    d.n_pad = B.n_pad;
+    d.n_kb = P.n_kb;
+    d.n_ch = P.n_ch;
+    items += (long long)d.n_tiles * P.n_ch;
+    if (P.n_ch > max_ch) max_ch = P.n_ch;
+    if (d.n_tiles < min_tiles) min_tiles = d.n_tiles;
+    prep_cols_kernel<<<P.n_ch, CHR, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
+                                                 const_cast<float*>(d.wmax), d_err);
+    prep_rows_kernel<<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(B.Z, B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
+                                                                 const_cast<uint8_t*>(d.aplanes),
+                                                                 const_cast<float2*>(d.braw), const_cast<float*>(d.zmax),
+                                                                 const_cast<int*>(d.expA));
+  }
+  a.total_items = items;
+  // one persistent CTA per SM; every CTA's range must hold at least one tile's chunks of any block
+  long long grid = s.n_sm;
+  if (items / max_ch < grid) grid = items / max_ch;
+  if (grid < 1) grid = 1;
+  const size_t smem = main_smem_bytes(N, TJ, L);
+  herk_mixed_kernel<<<(int)grid, NTHREADS, smem, stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
+}
+
+qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, int n_pb, int n_pad, int n_occ,
+                             int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
+                             int* d_err, cudaStream_t stream) {
+  MixedBlock b{Z, ldz, n_pb, n_pad, n_occ, n_unocc, eo, eu, acc};
+  return mixed_accumulate_batch(s, 1, &b, g, d_err, stream);
 }
 
 void mixed_free(MixedScratch& s) {
   if (s.planes) cudaFree(s.planes);
-  if (s.aux) cudaFree(s.aux);
+  for (auto& e : s.tile_lists) cudaFree(e.tiles);
   s = MixedScratch{};
 }
 

@@ -28,7 +28,14 @@ QSGW_MIXED_BF16X3 = 1
 EXPORTS = [
     "qsgw_chi0_init", "qsgw_chi0_accumulate", "qsgw_chi0_finalize", "qsgw_eps_inv", "qsgw_chi0_reset",
     "qsgw_chi0_sync", "qsgw_chi0_destroy", "qsgw_status_string", "qsgw_synth_z", "qsgw_chi0_accumulate_synthetic",
+    "qsgw_chi0_accumulate_batch",
 ]
+
+
+class qsgw_block(ctypes.Structure):
+    """C struct qsgw_block (include/qsgw.h)."""
+    _fields_ = [("q", ctypes.c_int), ("Z", ctypes.c_void_p), ("ldz", ctypes.c_longlong), ("n_occ", ctypes.c_int),
+                ("n_unocc", ctypes.c_int), ("eps_occ", ctypes.c_void_p), ("eps_unocc", ctypes.c_void_p)]
 
 
 class QsgwError(RuntimeError):
@@ -60,6 +67,7 @@ def load():
         "qsgw_chi0_destroy": [_p],
         "qsgw_synth_z": [_u64, _i, _i, _i, _i, _i, _d, _p, _ll, _p],
         "qsgw_chi0_accumulate_synthetic": [_p, _i, _u64, _i, _i, _i, _i, P(_i), _p, _p, _d],
+        "qsgw_chi0_accumulate_batch": [_p, _i, P(qsgw_block)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -157,3 +165,12 @@ def qsgw_chi0_accumulate_synthetic(ctx: int, q: int, seed: int, gen_q: int, k_be
     _check(load().qsgw_chi0_accumulate_synthetic(ctx, q, int(seed), int(gen_q), int(k_begin), int(k_end), int(n_occ),
                                                  arr, _addr(eps_occ), _addr(eps_unocc), float(s_div)),
            "qsgw_chi0_accumulate_synthetic")
+
+
+def qsgw_chi0_accumulate_batch(ctx: int, blocks):
+    """blocks: iterable of (q, Z, ldz, n_occ, n_unocc, eps_occ, eps_unocc) with device arrays."""
+    blocks = list(blocks)
+    arr = (qsgw_block * len(blocks))()
+    for i, (q, Z, ldz, n_occ, n_unocc, eo, eu) in enumerate(blocks):
+        arr[i] = qsgw_block(int(q), _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eo), _addr(eu))
+    _check(load().qsgw_chi0_accumulate_batch(ctx, len(blocks), arr), "qsgw_chi0_accumulate_batch")
