@@ -11,16 +11,18 @@
 namespace qsgw {
 
 // Accumulator element (I, J) of frequency l, `loc` = J * n_pad + I.
-// ACC_FP64: double2 [l][J][I]. ACC_DF32: two copies of float2 (hi, lo) planes [l][re|im][J][I].
+// ACC_FP64: double2 [l][J][I]. ACC_DF32: float2 (hi, lo) planes [l][re|im][J][I], then an FP64
+// buffer of the same layout (pieces of split tiles).
 template <int KIND>
 __device__ __forceinline__ double2 load_acc(const void* acc, int l, size_t loc, int n_pad) {
   const size_t nn = (size_t)n_pad * n_pad;
   if (KIND == ACC_FP64) return static_cast<const double2*>(acc)[(size_t)l * nn + loc];
   const float2* a = static_cast<const float2*>(acc) + (size_t)l * 2 * nn + loc;
-  const float2* b = a + (size_t)gridDim.z * 2 * nn;  // second copy (gridDim.z = number of frequencies)
-  const float2 re = a[0], im = a[nn], re2 = b[0], im2 = b[nn];
-  return make_double2(((double)re.x + (double)re.y) + ((double)re2.x + (double)re2.y),
-                      ((double)im.x + (double)im.y) + ((double)im2.x + (double)im2.y));
+  // FP64 buffer of the split tiles after the double-float one (gridDim.z = number of frequencies)
+  const double* b = reinterpret_cast<const double*>(static_cast<const float2*>(acc) + (size_t)gridDim.z * 2 * nn) +
+                    (size_t)l * 2 * nn + loc;
+  const float2 re = a[0], im = a[nn];
+  return make_double2(((double)re.x + (double)re.y) + b[0], ((double)im.x + (double)im.y) + b[nn]);
 }
 
 // MODE 0: out = chi0. MODE 1: out = eps. Grid (n/32 J-blocks, n/32 I-blocks, L), block (32, 8).

@@ -203,26 +203,63 @@ struct BlockDesc {
   const int* expA;
   const float* wmax;
   const int2* tiles;
-  float2* acc;   // [l][part][J][I] (hi, lo): chunks of a tile processed by the tile's first CTA
-  float2* acc2;  // same layout: chunks of a tile whose first chunk belongs to the previous CTA
-  long long item_off;  // first (tile, chunk) item of this block in the launch's item list
+  float2* acc;    // [l][part][J][I] (hi, lo): whole tiles, each owned by one CTA
+  double* acc2;   // [l][part][J][I] FP64: pieces of the last tiles, added with atomics
+  int tile_off;   // first global tile index of this block
   int n_pb, n_pad, n_kb, n_tiles, n_ch;
 };
 constexpr int kMaxBlocks = 32;  // blocks per launch (descriptors travel by value as kernel parameters)
 
+// Work schedule. The T tiles of all blocks (block-major, then tile-major, so consecutive tiles share
+// their row operand) are handed out whole through a global counter, so the CTAs run through them in
+// near lockstep and the row-operand planes of a K-block are read from HBM once and served to the
+// other CTAs of that row tile from L2. The last R tiles (R = T mod #CTAs, or all tiles if T is
+// smaller) are cut into P chunk ranges each, so the final wave keeps every SM busy; such pieces
+// are added to the FP64 accumulator with atomics.
 struct MainArgs {
   BlockDesc blk[kMaxBlocks];
   int nb;
-  long long total_items;
+  int T, T_whole, P, n_items;
+  int* counter;
   int L, TJ, N;
   uint32_t idesc;
   int* d_err;
 };
 
-// Block that holds `item`, searching forward from `b` (items are visited in increasing order).
-__device__ __forceinline__ int block_of(const BlockDesc* blk, int nb, int b, long long item) {
-  while (b + 1 < nb && blk[b + 1].item_off <= item) ++b;
+struct WorkItem {
+  int gt;      // global tile index, -1 = none
+  int c0, c1;  // chunk range
+  int flags;   // bit 0: last item of this CTA; bit 1: piece (FP64 atomics)
+};
+constexpr int kRing = 4;
+
+__device__ __forceinline__ int block_of_tile(const BlockDesc* blk, int nb, int gt) {
+  int b = 0;
+  while (b + 1 < nb && blk[b + 1].tile_off <= gt) ++b;
   return b;
+}
+
+__device__ WorkItem decode_item(const MainArgs& p, const BlockDesc* blk, int i) {
+  WorkItem w;
+  w.gt = -1;
+  w.c0 = w.c1 = 0;
+  w.flags = 0;
+  if (i >= p.n_items) return w;
+  if (i < p.T_whole) {
+    w.gt = i;
+    const BlockDesc& bd = blk[block_of_tile(blk, p.nb, i)];
+    w.c0 = 0;
+    w.c1 = bd.n_ch;
+    return w;
+  }
+  const int j = i - p.T_whole;
+  w.gt = p.T_whole + j / p.P;
+  const int piece = j % p.P;
+  const BlockDesc& bd = blk[block_of_tile(blk, p.nb, w.gt)];
+  w.c0 = piece * bd.n_ch / p.P;
+  w.c1 = (piece + 1) * bd.n_ch / p.P;
+  w.flags = 2;
+  return w;
 }
 
 __device__ __forceinline__ void df_add(float2& v, float x) {
@@ -235,7 +272,8 @@ __device__ __forceinline__ void df_add(float2& v, float x) {
 
 __host__ __device__ constexpr size_t main_smem_bytes(int N, int TJ, int L) {
   return 1024 + (size_t)NS * A_STAGE + (size_t)NSB * 3 * 64 * N + (size_t)NS * KBR * TJ * 8 +
-         (size_t)NS * KBR * L * 4 + 256 * 4 * 2 + 32 * 8 + 64 + sizeof(BlockDesc) * kMaxBlocks;
+         (size_t)NS * KBR * L * 4 + 256 * 4 * 2 + 32 * 8 + 64 + sizeof(BlockDesc) * kMaxBlocks +
+         sizeof(WorkItem) * kRing;
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
@@ -259,10 +297,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint64_t* accempty = accfull + 1;  // 8 epilogue warps -> MMA
   uint64_t* finbar = accempty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(finbar + 1);
-  int* abortP = reinterpret_cast<int*>(tmem_slot + 1);
+  int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [2] builder-warp failure flags, by chunk parity
   BlockDesc* sBlk = reinterpret_cast<BlockDesc*>(bars + 32);  // block table, copied from the parameters
+  WorkItem* ring = reinterpret_cast<WorkItem*>(sBlk + kMaxBlocks);  // items in flight, producer -> others
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < p.nb; i += NTHREADS) sBlk[i] = p.blk[i];
+  int next_i = 0;  // producer thread only: the next item index it grabbed
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
@@ -275,92 +316,114 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     mbar_init(accfull, 1);
     mbar_init(accempty, NBG / 32);
     mbar_init(finbar, 1);
-    *abortP = 0;
+    abortB[0] = abortB[1] = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
-  for (int i = tid; i < p.nb; i += NTHREADS) sBlk[i] = p.blk[i];
+  __syncthreads();  // block table in shared memory
+  if (tid == 0) {   // first item (and whether it is the last) before the roles split
+    WorkItem w = decode_item(p, sBlk, atomicAdd(p.counter, 1));
+    next_i = atomicAdd(p.counter, 1);
+    if (w.gt >= 0 && next_i >= p.n_items) w.flags |= 1;
+    ring[0] = w;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // Persistent schedule: the (block, tile, chunk) items, block- then tile-major, are split into
-  // gridDim.x contiguous ranges of equal length (each >= one tile's chunks of any block, so a tile
-  // spans at most two CTAs). g counts this CTA's K-blocks; item = beg + g / KB_PER_CH.
-  const long long total = p.total_items;
-  const long long beg = total * blockIdx.x / gridDim.x, end = total * (blockIdx.x + 1) / gridDim.x;
-  const int n_g = (int)(end - beg) * KB_PER_CH;
-  const int nb = p.nb;
 
   if (warp == 0) {
-    // ---------------- producer: bulk copies of the A digit planes, raw B values and weights
+    // ---------------- producer: grabs items; bulk copies of A digit planes, raw B values, weights
     if (lane == 0) {
       const uint32_t raw_bytes = KBR * TJ * 8, w_bytes = KBR * L * 4;
-      int issued = 0, b = 0;
-      for (int g = 0; g < n_g; ++g) {
-        const int s = g % NS, round = g / NS;
-        const long long item = beg + g / KB_PER_CH;
-        b = block_of(sBlk, nb, b, item);
-        const BlockDesc& bd = sBlk[b];
-        const long long li = item - bd.item_off;
-        const int2 tile = bd.tiles[li / bd.n_ch];
-        const int kb = (int)(li % bd.n_ch) * KB_PER_CH + g % KB_PER_CH;
-        if (g >= NS && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitNs)) {
-          *abortP = 1;
-          atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
-          break;
+      int issued = 0, g = 0, pos = 0;
+      WorkItem cur = ring[0];
+      bool stop = cur.gt < 0;
+      while (!stop) {
+        const BlockDesc& bd = sBlk[block_of_tile(sBlk, p.nb, cur.gt)];
+        const int2 tile = bd.tiles[cur.gt - bd.tile_off];
+        const int nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+        for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
+          const int s = g % NS, round = g / NS;
+          const int kb = cur.c0 * KB_PER_CH + kbi;
+          if (g >= NS && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitNs)) {
+            atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+            stop = true;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], A_STAGE + raw_bytes + w_bytes);
+          bulk_g2s(sA + s * A_STAGE, bd.aplanes + ((size_t)tile.x * bd.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
+          bulk_g2s(sRaw + s * KBR * TJ, bd.braw + ((size_t)tile.y * bd.n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
+          bulk_g2s(sW + s * KBR * L, bd.wst + (size_t)kb * KBR * L, w_bytes, &full[s]);
+          issued = g + 1;
         }
-        mbar_arrive_expect_tx(&full[s], A_STAGE + raw_bytes + w_bytes);
-        bulk_g2s(sA + s * A_STAGE, bd.aplanes + ((size_t)tile.x * bd.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
-        bulk_g2s(sRaw + s * KBR * TJ, bd.braw + ((size_t)tile.y * bd.n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
-        bulk_g2s(sW + s * KBR * L, bd.wst + (size_t)kb * KBR * L, w_bytes, &full[s]);
-        issued = g + 1;
+        if (stop || (cur.flags & 1)) break;
+        // publish the next item before the arrive of its first K-block (release orders the store)
+        WorkItem nx = decode_item(p, sBlk, next_i);
+        next_i = atomicAdd(p.counter, 1);
+        if (next_i >= p.n_items) nx.flags |= 1;
+        ++pos;
+        ring[pos % kRing] = nx;
+        cur = nx;
       }
       // never leave a bulk copy in flight into shared memory at exit
-      for (int g = (issued > NS ? issued - NS : 0); g < issued; ++g)
-        mbar_wait_bounded(&full[g % NS], (g / NS) & 1, kWaitNs);
+      for (int k = (issued > NS ? issued - NS : 0); k < issued; ++k)
+        mbar_wait_bounded(&full[k % NS], (k / NS) & 1, kWaitNs);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
       const uint32_t idesc = p.idesc;
-      for (int g = 0; g < n_g; ++g) {
-        const int s = g % NS, sb = g % NSB, kbl = g % KB_PER_CH;
-        bool ok = mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
-        ok = ok && mbar_wait_bounded(&bfull[sb], (g / NSB) & 1, kWaitNs);
-        if (ok && kbl == 0 && g > 0) ok = mbar_wait_bounded(accempty, ((g / KB_PER_CH) - 1) & 1, kWaitNs);
-        if (!ok) {
-          *abortP = 1;
-          atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t a_base = smem_u32(sA + s * A_STAGE), b_base = smem_u32(sB + sb * BSTAGE);
+      int g = 0, pos = 0, lc = 0;  // lc: chunks started by this CTA
+      WorkItem cur = ring[0];
+      bool stop = cur.gt < 0;
+      while (!stop) {
+        int nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+        for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
+          const int s = g % NS, sb = g % NSB, kbl = kbi % KB_PER_CH;
+          bool ok = mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
+          if (ok && kbi == 0 && pos > 0) {  // the item was published before this K-block's copies
+            cur = ring[pos % kRing];
+            nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+          }
+          ok = ok && mbar_wait_bounded(&bfull[sb], (g / NSB) & 1, kWaitNs);
+          if (ok && kbl == 0 && lc > 0) ok = mbar_wait_bounded(accempty, (lc - 1) & 1, kWaitNs);
+          if (!ok) {
+            atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+            stop = true;
+            break;
+          }
+          if (kbl == 0) ++lc;
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(sA + s * A_STAGE), b_base = smem_u32(sB + sb * BSTAGE);
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          const uint32_t ao = a_base + ks * 4096, bo = b_base + ks * 32 * N;
-          const uint64_t a0 = make_smem_desc(ao, 2048, 128, 0);
-          const uint64_t a1 = make_smem_desc(ao + A_PLANE, 2048, 128, 0);
-          const uint64_t a2 = make_smem_desc(ao + 2 * A_PLANE, 2048, 128, 0);
-          const uint64_t b0 = make_smem_desc(bo, 16 * N, 128, 0);
-          const uint64_t b1 = make_smem_desc(bo + BPLANE, 16 * N, 128, 0);
-          const uint64_t b2 = make_smem_desc(bo + 2 * BPLANE, 16 * N, 128, 0);
-          const uint32_t acc_in = (kbl == 0 && ks == 0) ? 0u : 1u;
-          mma_bf16(tmem, a0, b0, idesc, acc_in);
-          mma_bf16(tmem + TMEM_L12, a0, b1, idesc, acc_in);
-          mma_bf16(tmem + TMEM_L12, a1, b0, idesc, 1u);
-          mma_bf16(tmem + TMEM_L12, a0, b2, idesc, 1u);
-          mma_bf16(tmem + TMEM_L12, a2, b0, idesc, 1u);
-          mma_bf16(tmem + TMEM_L12, a1, b1, idesc, 1u);
-          mma_bf16(tmem + TMEM_L12, a1, b2, idesc, 1u);
-          mma_bf16(tmem + TMEM_L12, a2, b1, idesc, 1u);
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t ao = a_base + ks * 4096, bo = b_base + ks * 32 * N;
+            const uint64_t a0 = make_smem_desc(ao, 2048, 128, 0);
+            const uint64_t a1 = make_smem_desc(ao + A_PLANE, 2048, 128, 0);
+            const uint64_t a2 = make_smem_desc(ao + 2 * A_PLANE, 2048, 128, 0);
+            const uint64_t b0 = make_smem_desc(bo, 16 * N, 128, 0);
+            const uint64_t b1 = make_smem_desc(bo + BPLANE, 16 * N, 128, 0);
+            const uint64_t b2 = make_smem_desc(bo + 2 * BPLANE, 16 * N, 128, 0);
+            const uint32_t acc_in = (kbl == 0 && ks == 0) ? 0u : 1u;
+            mma_bf16(tmem, a0, b0, idesc, acc_in);
+            mma_bf16(tmem + TMEM_L12, a0, b1, idesc, acc_in);
+            mma_bf16(tmem + TMEM_L12, a1, b0, idesc, 1u);
+            mma_bf16(tmem + TMEM_L12, a0, b2, idesc, 1u);
+            mma_bf16(tmem + TMEM_L12, a2, b0, idesc, 1u);
+            mma_bf16(tmem + TMEM_L12, a1, b1, idesc, 1u);
+            mma_bf16(tmem + TMEM_L12, a1, b2, idesc, 1u);
+            mma_bf16(tmem + TMEM_L12, a2, b1, idesc, 1u);
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&bempty[sb]);
+          if (kbl == KB_PER_CH - 1) mma_commit(accfull);
         }
-        mma_commit(&empty[s]);
-        mma_commit(&bempty[sb]);
-        if (kbl == KB_PER_CH - 1) mma_commit(accfull);
+        if (stop || (cur.flags & 1)) break;
+        ++pos;
       }
       // drain: all issued MMAs complete before TMEM is released
       mma_commit(finbar);
@@ -379,125 +442,159 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     const int boff = (bn >> 3) * 128 + (bn & 7) * 16;
     float bsc = 0.f;
     bool bjok = false;
-    int it = 0, jt = 0, c = 0, b = 0;
-    bool second = false;
-    // A warp whose wait timed out keeps iterating without waits or work ("dead"), so every named
-    // barrier below is still reached by all builder threads; dead is warp-uniform, as the
-    // warp-collective TMEM loads require.
+    int it = 0, jt = 0, b = 0;
+    // A warp whose wait timed out ("dead", warp-uniform) skips waits and work for the rest of its
+    // chunk and sets abortB[chunk parity]; at that chunk's epilogue barrier every builder warp reads
+    // the flag and all leave together, so no named barrier is ever left short of a warp. (Items end
+    // on chunk boundaries, so no warp reads the item ring after a failure.)
     bool dead = false;
-    for (int g = 0; g < n_g; ++g) {
-      const int s = g % NS, sb = g % NSB, kbl = g % KB_PER_CH, lc = g / KB_PER_CH;
-      if (kbl == 0) {  // new (block, tile, chunk) item
-        const long long item = beg + lc;
-        b = block_of(sBlk, nb, b, item);
+    int g = 0, pos = 0, lc = 0;
+    WorkItem cur = ring[0];
+    bool more = cur.gt >= 0;
+    while (more) {
+      int nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+      for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
+        const int s = g % NS, sb = g % NSB, kbl = kbi % KB_PER_CH;
+        bool ok = !dead && mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
+        if (ok && g >= NSB) ok = mbar_wait_bounded(&bempty[sb], ((g / NSB) - 1) & 1, kWaitNs);
+        if (!dead && __any_sync(0xffffffffu, !ok)) {
+          dead = true;
+          if (lane == 0) {
+            abortB[lc & 1] = 1;
+            atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+          }
+        }
+        if (kbi == 0) {  // new item: published before this K-block's copies (or before the roles split)
+          if (pos > 0) {
+            cur = ring[pos % kRing];
+            nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+          }
+          b = block_of_tile(sBlk, p.nb, cur.gt);
+          const int2 tile = sBlk[b].tiles[cur.gt - sBlk[b].tile_off];
+          it = tile.x;
+          jt = tile.y;
+          bjok = has_row && (jt * TJ + bj < sBlk[b].n_pb);
+        }
         const BlockDesc& bd = sBlk[b];
-        const long long li = item - bd.item_off;
-        const int t = (int)(li / bd.n_ch);
-        const int2 tile = bd.tiles[t];
-        it = tile.x;
-        jt = tile.y;
-        c = (int)(li % bd.n_ch);
-        second = bd.item_off + (long long)t * bd.n_ch < beg;
-        bjok = has_row && (jt * TJ + bj < bd.n_pb);
-        if (has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
+        const int c = cur.c0 + kbi / KB_PER_CH;
+        if (kbl == 0 && has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
           const float zm = bjok ? bd.zmax[(size_t)c * bd.n_pad + jt * TJ + bj] : 0.f;
           const int e = scale_exp(bd.wmax[c * L + bl] * zm);
           sExpB[bn] = e;
           bsc = exp2i(e);
         }
-      }
-      bool ok = !dead && mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
-      if (ok && g >= NSB) ok = mbar_wait_bounded(&bempty[sb], ((g / NSB) - 1) & 1, kWaitNs);
-      if (!dead && __any_sync(0xffffffffu, !ok)) {
-        dead = true;
-        atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
-      }
-      if (has_row && !dead) {
-        const float2* raw = sRaw + s * KBR * TJ + bj;
-        const float* ws = sW + s * KBR * L + bl;
-        uint8_t* bdst = sB + sb * BSTAGE + boff;
+        if (has_row && !dead) {
+          const float2* raw = sRaw + s * KBR * TJ + bj;
+          const float* ws = sW + s * KBR * L + bl;
+          uint8_t* bdst = sB + sb * BSTAGE + boff;
 #pragma unroll
-        for (int kg = 0; kg < 4; ++kg) {
-          float d[3][8];
+          for (int kg = 0; kg < 4; ++kg) {
+            float d[3][8];
 #pragma unroll
-          for (int rr = 0; rr < 4; ++rr) {
-            const int rl = kg * 4 + rr;
-            const float2 z = bjok ? raw[rl * TJ] : make_float2(0.f, 0.f);
-            const float ww = ws[rl * L] * bsc;
-            digits3(ww * z.x, d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
-            digits3(ww * z.y, d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
-          }
+            for (int rr = 0; rr < 4; ++rr) {
+              const int rl = kg * 4 + rr;
+              const float2 z = bjok ? raw[rl * TJ] : make_float2(0.f, 0.f);
+              const float ww = ws[rl * L] * bsc;
+              digits3(ww * z.x, d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
+              digits3(ww * z.y, d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
+            }
 #pragma unroll
-          for (int pl = 0; pl < 3; ++pl) {
-            uint4 v;
-            v.x = pack_bf16(d[pl][0], d[pl][1]);
-            v.y = pack_bf16(d[pl][2], d[pl][3]);
-            v.z = pack_bf16(d[pl][4], d[pl][5]);
-            v.w = pack_bf16(d[pl][6], d[pl][7]);
-            *reinterpret_cast<uint4*>(bdst + pl * BPLANE + kg * 16 * N) = v;
-          }
-        }
-      }
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0 && !dead) {
-        mbar_arrive(&bfull[sb]);
-        mbar_arrive(&empty[s]);
-      }
-      if (kbl == KB_PER_CH - 1) {
-        // ------------- chunk epilogue: TMEM -> registers -> scaled -> double-float global accumulator
-        ok = !dead && mbar_wait_bounded(accfull, lc & 1, kWaitNs);
-        if (!dead && __any_sync(0xffffffffu, !ok)) {
-          dead = true;
-          atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
-        }
-        named_bar_sync(1, NBG);  // the chunk's exponent table (written at chunk start) is complete
-        tc_fence_after();
-        const BlockDesc& bd = sBlk[b];
-        const int I = it * TI + (m_row % TI);
-        const int eA = bd.expA[(size_t)c * bd.n_pad + I];
-        const bool iok = I < bd.n_pb;
-        const int half = N / 2;  // a multiple of 8
-        const size_t nn = (size_t)bd.n_pad * bd.n_pad;
-        float2* accI = (second ? bd.acc2 : bd.acc) + (size_t)part * nn + I;
-        const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        const int col_end = dead ? wg * half : (wg + 1) * half;  // a dead warp skips the flush
-        for (int col0 = wg * half; col0 < col_end; col0 += 16) {
-          const int cnt = min(16, col_end - col0);  // 16 or 8
-          uint32_t r0[16], r1[16];
-          tmem_ld_x8(tl + col0, *reinterpret_cast<uint32_t(*)[8]>(&r0[0]));
-          tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
-          if (cnt == 16) {
-            tmem_ld_x8(tl + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r0[8]));
-            tmem_ld_x8(tl + TMEM_L12 + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r1[8]));
-          }
-          tmem_ld_wait();
-          // all global loads of the group first (independent), then the double-float adds and stores
-          float2 v[16];
-          size_t off[16];
-          bool okc[16];
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
-            okc[jj] = jj < cnt && iok && J < bd.n_pb;
-            off[jj] = (size_t)l * 2 * nn + (size_t)J * bd.n_pad;
-            if (okc[jj]) v[jj] = accI[off[jj]];
-          }
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            if (okc[jj]) {
-              const float sc = exp2i(-(eA + sExpB[col0 + jj]));
-              df_add(v[jj], __uint_as_float(r0[jj]) * sc);
-              df_add(v[jj], __uint_as_float(r1[jj]) * sc);
-              accI[off[jj]] = v[jj];
+            for (int pl = 0; pl < 3; ++pl) {
+              uint4 v;
+              v.x = pack_bf16(d[pl][0], d[pl][1]);
+              v.y = pack_bf16(d[pl][2], d[pl][3]);
+              v.z = pack_bf16(d[pl][4], d[pl][5]);
+              v.w = pack_bf16(d[pl][6], d[pl][7]);
+              *reinterpret_cast<uint4*>(bdst + pl * BPLANE + kg * 16 * N) = v;
             }
           }
         }
-        tc_fence_before();
+        fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0 && !dead) mbar_arrive(accempty);
-        named_bar_sync(1, NBG);  // exponent table of this chunk no longer needed
+        if (lane == 0 && !dead) {
+          mbar_arrive(&bfull[sb]);
+          mbar_arrive(&empty[s]);
+        }
+        if (kbl == KB_PER_CH - 1) {
+          // ------------- chunk epilogue: TMEM -> registers -> scaled -> global accumulator
+          ok = !dead && mbar_wait_bounded(accfull, lc & 1, kWaitNs);
+          if (!dead && __any_sync(0xffffffffu, !ok)) {
+            dead = true;
+            if (lane == 0) {
+              abortB[lc & 1] = 1;
+              atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+            }
+          }
+          named_bar_sync(1, NBG);  // the chunk's exponent table (written at chunk start) is complete
+          if (abortB[lc & 1]) {    // some builder warp failed in this chunk: all leave together
+            more = false;
+            break;
+          }
+          ++lc;
+          tc_fence_after();
+          const int I = it * TI + (m_row % TI);
+          const int eA = bd.expA[(size_t)c * bd.n_pad + I];
+          const bool iok = I < bd.n_pb;
+          const bool piece = (cur.flags & 2) != 0;
+          const int half = N / 2;  // a multiple of 8
+          const size_t nn = (size_t)bd.n_pad * bd.n_pad;
+          const size_t base = (size_t)part * nn + I;
+          const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+          const int col_end = (wg + 1) * half;
+          for (int col0 = wg * half; col0 < col_end; col0 += 16) {
+            const int cnt = min(16, col_end - col0);  // 16 or 8
+            uint32_t r0[16], r1[16];
+            tmem_ld_x8(tl + col0, *reinterpret_cast<uint32_t(*)[8]>(&r0[0]));
+            tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
+            if (cnt == 16) {
+              tmem_ld_x8(tl + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r0[8]));
+              tmem_ld_x8(tl + TMEM_L12 + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r1[8]));
+            }
+            tmem_ld_wait();
+            if (piece) {
+              // a piece of a split tile: FP64 atomics into the second accumulator
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
+                if (jj < cnt && iok && J < bd.n_pb) {
+                  const double sc = (double)exp2i(-(eA + sExpB[n]));
+                  const double x = ((double)__uint_as_float(r0[jj]) + (double)__uint_as_float(r1[jj])) * sc;
+                  atomicAdd(bd.acc2 + base + (size_t)l * 2 * nn + (size_t)J * bd.n_pad, x);
+                }
+              }
+              continue;
+            }
+            // all global loads of the group first (independent), then the double-float adds and stores
+            float2* accI = bd.acc + base;
+            float2 v[16];
+            uint32_t okc = 0;
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
+              if (jj < cnt && iok && J < bd.n_pb) {
+                okc |= 1u << jj;
+                v[jj] = accI[(size_t)l * 2 * nn + (size_t)J * bd.n_pad];
+              }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              if (okc & (1u << jj)) {
+                const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
+                const float sc = exp2i(-(eA + sExpB[n]));
+                df_add(v[jj], __uint_as_float(r0[jj]) * sc);
+                df_add(v[jj], __uint_as_float(r1[jj]) * sc);
+                accI[(size_t)l * 2 * nn + (size_t)J * bd.n_pad] = v[jj];
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(accempty);
+          named_bar_sync(1, NBG);  // exponent table of this chunk no longer needed
+        }
       }
+      more = more && !(cur.flags & 1);
+      ++pos;
     }
   }
   tc_fence_before();
@@ -604,8 +701,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
   a.d_err = d_err;
   uint8_t* base = static_cast<uint8_t*>(s.planes);
-  long long items = 0;
-  int max_ch = 1, min_tiles = 1 << 30;
+  int T = 0, min_ch_tail = 1 << 30;
   for (int b = 0; b < nb; ++b) {
     const Plan& P = pl[b];
     const MixedBlock& B = in[b];
@@ -619,15 +715,13 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     d.expA = reinterpret_cast<int*>(base + P.o_exp);
     d.wmax = reinterpret_cast<float*>(base + P.o_wmax);
     d.acc = reinterpret_cast<float2*>(B.acc);
-    d.acc2 = d.acc + (size_t)L * 2 * B.n_pad * B.n_pad;
-    d.item_off = items;
+    d.acc2 = reinterpret_cast<double*>(d.acc + (size_t)L * 2 * B.n_pad * B.n_pad);
+    d.tile_off = T;
     d.n_pb = B.n_pb;
     d.n_pad = B.n_pad;
     d.n_kb = P.n_kb;
     d.n_ch = P.n_ch;
-    items += (long long)d.n_tiles * P.n_ch;
-    if (P.n_ch > max_ch) max_ch = P.n_ch;
-    if (d.n_tiles < min_tiles) min_tiles = d.n_tiles;
+    T += d.n_tiles;
     prep_cols_kernel<<<P.n_ch, CHR, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
                                                  const_cast<float*>(d.wmax), d_err);
     prep_rows_kernel<<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(B.Z, B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
@@ -635,13 +729,26 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
                                                                  const_cast<float2*>(d.braw), const_cast<float*>(d.zmax),
                                                                  const_cast<int*>(d.expA));
   }
-  a.total_items = items;
-  // one persistent CTA per SM; every CTA's range must hold at least one tile's chunks of any block
-  long long grid = s.n_sm;
-  if (items / max_ch < grid) grid = items / max_ch;
-  if (grid < 1) grid = 1;
+  // whole tiles first; the last R tiles (a partial last wave) are split into P chunk ranges
+  const int G = s.n_sm;
+  const int R = T >= G ? T % G : T;
+  a.T = T;
+  a.T_whole = T - R;
+  for (int b = 0; b < nb; ++b) {  // smallest chunk count among blocks that own tail tiles
+    const BlockDesc& d = a.blk[b];
+    if (d.tile_off + d.n_tiles > a.T_whole && d.n_ch < min_ch_tail) min_ch_tail = d.n_ch;
+  }
+  int P = R > 0 ? G / R : 1;
+  if (P < 1) P = 1;
+  if (R > 0 && P > min_ch_tail) P = min_ch_tail;
+  a.P = P;
+  a.n_items = a.T_whole + R * P;
+  if (!s.counter && cudaMalloc(&s.counter, sizeof(int)) != cudaSuccess) return QSGW_ERR_NOMEM;
+  a.counter = s.counter;
+  if (cudaMemsetAsync(s.counter, 0, sizeof(int), stream) != cudaSuccess) return QSGW_ERR_CUDA;
+  const int grid = a.n_items < G ? a.n_items : G;
   const size_t smem = main_smem_bytes(N, TJ, L);
-  herk_mixed_kernel<<<(int)grid, NTHREADS, smem, stream>>>(a);
+  herk_mixed_kernel<<<grid, NTHREADS, smem, stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
 }
 
@@ -654,6 +761,7 @@ qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, i
 
 void mixed_free(MixedScratch& s) {
   if (s.planes) cudaFree(s.planes);
+  if (s.counter) cudaFree(s.counter);
   for (auto& e : s.tile_lists) cudaFree(e.tiles);
   s = MixedScratch{};
 }

@@ -19,11 +19,12 @@ struct MixedScratch {
   std::vector<TileList> tile_lists;
   bool attr_set = false;
   int n_sm = 0;
+  int* counter = nullptr;  // work-queue counter of the tensor-core launch
 };
 
-// One block of transition columns for one q-point. acc: the q-point's accumulator, two
-// double-float copies back to back, each float2 (hi, lo) planes [L][2 (re, im)][n_pad (J)][n_pad (I)];
-// chi0 is their sum.
+// One block of transition columns for one q-point. acc: the q-point's accumulator, a double-float
+// buffer (float2 (hi, lo) planes [L][2 (re, im)][n_pad (J)][n_pad (I)]) followed by an FP64 buffer
+// of the same layout for split tiles; chi0 is their sum.
 struct MixedBlock {
   const double2* Z;
   long long ldz;
