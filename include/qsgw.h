@@ -136,6 +136,31 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx *ctx);
 /* Static, human-readable name of a status code. */
 const char *qsgw_status_string(qsgw_status s);
 
+/* ---- allocation-free form (no counterpart in the paper) --------------------------------
+ * chi0 of ONE block of transition columns, computed in mixed precision exactly as
+ * qsgw_chi0_accumulate + qsgw_chi0_finalize would on a fresh context, but without allocating
+ * any device memory: every intermediate (digit planes, weights, tile list, accumulators, error
+ * flag) lives in one fixed 64 MiB array in the library's device image. It is for callers that
+ * cannot call cudaMalloc: code whose device memory is entirely reserved by another allocator
+ * (a framework's caching pool or a fixed arena), code that must not risk the implicit device
+ * synchronisation cudaMalloc/cudaFree may cause, and code paths that are not allowed to fail on
+ * an allocation at run time. Every GPU that loads the library holds the array until exit.
+ *   Z, eps_occ, eps_unocc  device; same meaning and layout as in qsgw_chi0_accumulate
+ *   n_omega, omega         host, as in qsgw_chi0_init (1..16 frequencies, omega_l >= 0)
+ *   spin_factor            s of the formula at the top of this file
+ *   chi0                   device complex128 [n_omega][n_pb][n_pb], overwritten with the full
+ *                          Hermitian chi0 of this block
+ *   cuda_stream            stream the work is ordered on; the call synchronises it at the end to
+ *                          return device-detected errors (QSGW_ERR_DOMAIN, QSGW_ERR_TIMEOUT)
+ * Sizes whose intermediates do not fit the fixed array return QSGW_ERR_ARG (use the context
+ * API instead); n_pb <= 256 with n_occ * n_unocc <= 3072 always fits. The first call on a
+ * device looks up the array's device address (and raises the kernel's shared-memory limit),
+ * so make that first call before any stream capture. All calls share the one array: calls
+ * whose GPU work overlaps (other streams, other host threads) race and must not be issued. */
+qsgw_status qsgw_chi0_block_noalloc(const void *Z, long long ldz, int n_pb, int n_occ, int n_unocc,
+                                    const double *eps_occ, const double *eps_unocc, int n_omega,
+                                    const double *omega, double spin_factor, void *chi0, void *cuda_stream);
+
 /* ---- synthetic inputs (not part of the paper's method) --------------------------------
  * The paper's Z comes from PMT eigenfunctions (Eq. (defz)), which are not available. These
  * entry points draw Z on the device from Philox4x32-10 with the same counter layout as the

@@ -353,6 +353,26 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   return st;
 }
 
+qsgw_status qsgw_chi0_block_noalloc(const void* Z, long long ldz, int n_pb, int n_occ, int n_unocc,
+                                    const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega,
+                                    double spin_factor, void* chi0, void* cuda_stream) {
+  if (!Z || !eps_occ || !eps_unocc || !omega || !chi0 || n_pb < 1 || n_pb > kMaxNpb || ldz < n_pb || n_occ < 1 ||
+      n_unocc < 1 || n_omega < 1 || n_omega > kMaxOmega || !std::isfinite(spin_factor))
+    return QSGW_ERR_ARG;
+  if ((long long)n_occ * n_unocc > (1LL << 31)) return QSGW_ERR_ARG;
+  OmegaGrid g{};
+  g.L = n_omega;
+  for (int l = 0; l < n_omega; ++l) {
+    if (!std::isfinite(omega[l]) || omega[l] < 0.0) return QSGW_ERR_ARG;
+    g.w2[l] = omega[l] * omega[l];
+    g.w2f[l] = (float)(omega[l] * omega[l]);
+  }
+  if (!is_device_ptr(Z) || !is_device_ptr(eps_occ) || !is_device_ptr(eps_unocc) || !is_device_ptr(chi0))
+    return QSGW_ERR_ARG;
+  return mixed_chi0_noalloc(static_cast<const double2*>(Z), ldz, n_pb, n_occ, n_unocc, eps_occ, eps_unocc, g,
+                            spin_factor, static_cast<double2*>(chi0), static_cast<cudaStream_t>(cuda_stream));
+}
+
 qsgw_status qsgw_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, int n_occ, int n_unocc, double s_div,
                          void* Z, long long ldz, void* cuda_stream) {
   if (!Z || n_pb < 1 || n_occ < 1 || n_unocc < 1 || ldz < n_pb || k < 0 || gen_q < 0 || gen_q > 0xFFFFFF ||

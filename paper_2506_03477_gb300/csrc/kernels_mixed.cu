@@ -759,6 +759,128 @@ qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, i
   return mixed_accumulate_batch(s, 1, &b, g, d_err, stream);
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+// One block of columns, chi0 written straight to the caller's buffer, every intermediate in a
+// fixed file-scope device array instead of cudaMalloc'd scratch. See qsgw_chi0_block_noalloc.
+constexpr size_t kNoAllocBytes = 64ull << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+constexpr int kMaxDevices = 64;
+static void* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// Upper-triangle tile list of one (n_pb, TJ), in the order tile_list() uses, built on the device.
+__global__ void noalloc_tiles_kernel(int n_pb, int n_it, int n_jt, int TJ, int2* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int k = 0;
+  for (int it = 0; it < n_it; ++it)
+    for (int jt = 0; jt < n_jt; ++jt)
+      if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) out[k++] = make_int2(it, jt);
+}
+
+qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_occ, int n_unocc, const double* eo,
+                               const double* eu, const OmegaGrid& g, double spin, double2* chi0, cudaStream_t stream) {
+  const int L = g.L, TJ = tile_width(L), N = TJ * L;
+  if (TJ < 1 || N < 16 || N > 256) return QSGW_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QSGW_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {  // set-up, once per device, with that device current
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return QSGW_ERR_CUDA;
+    if (cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+        cudaSuccess)
+      return QSGW_ERR_CUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QSGW_ERR_CUDA;
+  const int n_pad = pad_to(n_pb, kPad);
+  const long long K = (long long)n_occ * n_unocc;
+  const int n_ch = (int)((K + CHR - 1) / CHR), n_kb = n_ch * KB_PER_CH;
+  const int n_it = n_pad / TI, n_jt = (n_pb + TJ - 1) / TJ;
+  int n_tiles = 0;
+  for (int it = 0; it < n_it; ++it)
+    for (int jt = 0; jt < n_jt; ++jt)
+      if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) ++n_tiles;
+  // layout inside the fixed array
+  size_t off = 256;  // [0, 256): error flag, work counter
+  const size_t o_acc = off;
+  const size_t acc_bytes = (size_t)L * 2 * n_pad * n_pad * (sizeof(float2) + sizeof(double));
+  off += align256(acc_bytes);
+  const size_t o_tiles = off;
+  off += align256((size_t)n_tiles * sizeof(int2));
+  const size_t o_a = off;
+  off += align256((size_t)n_it * n_kb * A_STAGE);
+  const size_t o_raw = off;
+  off += align256((size_t)n_jt * n_kb * KBR * TJ * sizeof(float2));
+  const size_t o_w = off;
+  off += align256((size_t)n_kb * KBR * L * sizeof(float));
+  const size_t o_zmax = off;
+  off += align256((size_t)n_ch * n_pad * sizeof(float));
+  const size_t o_exp = off;
+  off += align256((size_t)n_ch * n_pad * sizeof(int));
+  const size_t o_wmax = off;
+  off += align256((size_t)n_ch * L * sizeof(float));
+  if (off > kNoAllocBytes) return QSGW_ERR_ARG;  // beyond the fixed array: use the context API
+  uint8_t* base = static_cast<uint8_t*>(g_noalloc_ptr[dev]);
+  int* d_err = reinterpret_cast<int*>(base);
+  int* counter = d_err + 1;
+  // the array keeps the previous call's contents: clear what must start at zero
+  if (cudaMemsetAsync(base, 0, 256, stream) != cudaSuccess) return QSGW_ERR_CUDA;
+  if (cudaMemsetAsync(base + o_acc, 0, acc_bytes, stream) != cudaSuccess) return QSGW_ERR_CUDA;
+  int2* tiles = reinterpret_cast<int2*>(base + o_tiles);
+  noalloc_tiles_kernel<<<1, 1, 0, stream>>>(n_pb, n_it, n_jt, TJ, tiles);
+
+  MainArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nb = 1;
+  a.L = L;
+  a.TJ = TJ;
+  a.N = N;
+  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
+  a.d_err = d_err;
+  BlockDesc& d = a.blk[0];
+  d.aplanes = base + o_a;
+  d.braw = reinterpret_cast<float2*>(base + o_raw);
+  d.wst = reinterpret_cast<float*>(base + o_w);
+  d.zmax = reinterpret_cast<float*>(base + o_zmax);
+  d.expA = reinterpret_cast<int*>(base + o_exp);
+  d.wmax = reinterpret_cast<float*>(base + o_wmax);
+  d.tiles = tiles;
+  d.acc = reinterpret_cast<float2*>(base + o_acc);
+  d.acc2 = reinterpret_cast<double*>(d.acc + (size_t)L * 2 * n_pad * n_pad);
+  d.tile_off = 0;
+  d.n_pb = n_pb;
+  d.n_pad = n_pad;
+  d.n_kb = n_kb;
+  d.n_tiles = n_tiles;
+  d.n_ch = n_ch;
+  prep_cols_kernel<<<n_ch, CHR, 0, stream>>>(eo, eu, n_unocc, K, g, const_cast<float*>(d.wst),
+                                            const_cast<float*>(d.wmax), d_err);
+  prep_rows_kernel<<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt,
+                                                          const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw),
+                                                          const_cast<float*>(d.zmax), const_cast<int*>(d.expA));
+  const int G = n_sm, T = n_tiles;
+  const int R = T >= G ? T % G : T;
+  a.T = T;
+  a.T_whole = T - R;
+  int P = R > 0 ? G / R : 1;
+  if (P < 1) P = 1;
+  if (R > 0 && P > n_ch) P = n_ch;
+  a.P = P;
+  a.n_items = a.T_whole + R * P;
+  a.counter = counter;
+  const int grid = a.n_items < G ? a.n_items : G;
+  herk_mixed_kernel<<<grid, NTHREADS, main_smem_bytes(N, TJ, L), stream>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return QSGW_ERR_CUDA;
+  launch_finalize_chi(d.acc, ACC_DF32, n_pb, n_pad, L, spin, chi0, stream);
+  int h_err = 0;
+  if (cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return QSGW_ERR_CUDA;
+  if (h_err == DEV_DOMAIN) return QSGW_ERR_DOMAIN;
+  if (h_err == DEV_TIMEOUT) return QSGW_ERR_TIMEOUT;
+  return QSGW_OK;
+}
+
 void mixed_free(MixedScratch& s) {
   if (s.planes) cudaFree(s.planes);
   if (s.counter) cudaFree(s.counter);

@@ -42,5 +42,8 @@ qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, i
                              int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
                              int* d_err, cudaStream_t stream);
 void mixed_free(MixedScratch& s);
+// chi0 of one block of columns into `chi0` using only a fixed file-scope device array (no allocation).
+qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_occ, int n_unocc, const double* eo,
+                               const double* eu, const OmegaGrid& g, double spin, double2* chi0, cudaStream_t stream);
 
 }  // namespace qsgw

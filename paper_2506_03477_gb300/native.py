@@ -28,7 +28,7 @@ QSGW_MIXED_BF16X3 = 1
 EXPORTS = [
     "qsgw_chi0_init", "qsgw_chi0_accumulate", "qsgw_chi0_finalize", "qsgw_eps_inv", "qsgw_chi0_reset",
     "qsgw_chi0_sync", "qsgw_chi0_destroy", "qsgw_status_string", "qsgw_synth_z", "qsgw_chi0_accumulate_synthetic",
-    "qsgw_chi0_accumulate_batch",
+    "qsgw_chi0_accumulate_batch", "qsgw_chi0_block_noalloc",
 ]
 
 
@@ -68,6 +68,7 @@ def load():
         "qsgw_synth_z": [_u64, _i, _i, _i, _i, _i, _d, _p, _ll, _p],
         "qsgw_chi0_accumulate_synthetic": [_p, _i, _u64, _i, _i, _i, _i, P(_i), _p, _p, _d],
         "qsgw_chi0_accumulate_batch": [_p, _i, P(qsgw_block)],
+        "qsgw_chi0_block_noalloc": [_p, _ll, _i, _i, _i, _p, _p, _i, P(_d), _d, _p, _p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -174,3 +175,13 @@ def qsgw_chi0_accumulate_batch(ctx: int, blocks):
     for i, (q, Z, ldz, n_occ, n_unocc, eo, eu) in enumerate(blocks):
         arr[i] = qsgw_block(int(q), _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eo), _addr(eu))
     _check(load().qsgw_chi0_accumulate_batch(ctx, len(blocks), arr), "qsgw_chi0_accumulate_batch")
+
+
+def qsgw_chi0_block_noalloc(Z, ldz: int, n_pb: int, n_occ: int, n_unocc: int, eps_occ, eps_unocc, omega,
+                            spin_factor: float, chi0, stream=None):
+    """chi0 of one block of columns into chi0 without any device allocation (see include/qsgw.h)."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    arr_o = (_d * om.size)(*om.tolist())
+    _check(load().qsgw_chi0_block_noalloc(_addr(Z), int(ldz), int(n_pb), int(n_occ), int(n_unocc), _addr(eps_occ),
+                                          _addr(eps_unocc), om.size, arr_o, float(spin_factor), _addr(chi0),
+                                          _stream(stream)), "qsgw_chi0_block_noalloc")
