@@ -37,6 +37,23 @@ F_STEP = 4.0 * K_COLS * N_PB * (N_PB + 1) * L
 CONFIG_NAME = "medium chi0+W: n_pb=1500, n_k=64, n_occ=40, n_unocc=400 (K=1,024,000), 12 imaginary frequencies"
 
 
+# DRAM traffic of one herk_mixed_kernel launch of this workload (one k-point), from the ncu
+# capture summarised in profiles/herk_mixed_kernel_medium_one_kpoint.md; valid only for the kernel
+# source it was measured on (sha1 prefix), otherwise reported as null.
+TRAFFIC_BYTES_PER_LAUNCH = 3.007e9
+TRAFFIC_KERNEL_SHA1 = "2c4f81d74e31"
+
+
+def measured_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2506_03477_gb300", "csrc", "kernels_mixed.cu")
+    try:
+        h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+    return TRAFFIC_BYTES_PER_LAUNCH if h == TRAFFIC_KERNEL_SHA1 else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -421,7 +438,7 @@ def main():
     issued = issued_mma_flops_per_call() if args.prec == "mixed" else None
     roof = {"bound": "tensor" if args.prec == "mixed" else "alu", "kernel": "herk_mixed_kernel (+ prep kernels in the timed call)",
             "achieved": achieved, "peak": sustained, "unit": "TFLOP/s", "frac": achieved / sustained,
-            "peak_source": f"{src} bf16 sustained", "traffic": None,
+            "peak_source": f"{src} bf16 sustained", "traffic": measured_traffic() if args.prec == "mixed" else None,
             "note": "achieved = algorithmic chi0 flops per accumulate call / CUDA-event duration of the call"}
     if issued:
         roof["tensor_pipe_issued_tflops"] = issued / (acc_avg * 1e-3) / 1e12
