@@ -40,8 +40,8 @@ CONFIG_NAME = "medium chi0+W: n_pb=1500, n_k=64, n_occ=40, n_unocc=400 (K=1,024,
 # DRAM traffic of one herk_mixed_kernel launch of this workload (one k-point), from the ncu
 # capture summarised in profiles/herk_mixed_kernel_medium_one_kpoint.md; valid only for the kernel
 # source it was measured on (sha1 prefix), otherwise reported as null.
-TRAFFIC_BYTES_PER_LAUNCH = 3.007e9
-TRAFFIC_KERNEL_SHA1 = "2c4f81d74e31"
+TRAFFIC_BYTES_PER_LAUNCH = 2.853e9
+TRAFFIC_KERNEL_SHA1 = "85e0b59e4e6d"
 
 
 def measured_traffic():
@@ -468,7 +468,7 @@ def issued_mma_flops_per_call():
     n_pad = (N_PB + 63) // 64 * 64
     n_it, n_jt = n_pad // 64, (N_PB + TJ - 1) // TJ
     tiles = sum(1 for it in range(n_it) for jt in range(n_jt) if jt * TJ + TJ - 1 >= it * 64 and it * 64 < N_PB)
-    n_kb = (N_OCC * N_UNOCC + 1023) // 1024 * 64
+    n_kb = (N_OCC * N_UNOCC + 15) // 16  # 16-column K-blocks (the last chunk stops at the last column)
     return tiles * n_kb * 2 * 8 * (2.0 * 128 * n * 16)
 
 

@@ -46,6 +46,14 @@ struct qsgw_ctx {
   size_t zstage_cap = 0;  // bytes
   double* d_estage = nullptr;
   size_t estage_cap = 0;  // doubles
+  // host Z: two device staging slots filled on a copy stream, so the copy of one block
+  // overlaps the kernels of the previous one
+  void* d_hstage[2] = {};
+  size_t hstage_cap[2] = {};  // bytes
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t hcopied[2] = {};  // slot filled (recorded on cstream)
+  cudaEvent_t hfree[2] = {};    // last reader of the slot done (recorded on stream)
+  int hslot = 0;
   MixedScratch mixed;
   SolverLane lanes[kMaxOmega];
   cudaEvent_t fork = nullptr;
@@ -209,15 +217,39 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ld
     eo = c->d_estage;
     eu = c->d_estage + n_occ;
   }
-  const double2* Zd = static_cast<const double2*>(Z);
-  if (!is_device_ptr(Z)) {
-    const size_t bytes = sizeof(double2) * (size_t)ldz * (size_t)K;
-    st = grow(&c->d_zstage, &c->zstage_cap, bytes);
-    if (st != QSGW_OK) return st;
-    QSGW_CK(cudaMemcpyAsync(c->d_zstage, Z, bytes, cudaMemcpyDefault, c->stream));
-    Zd = static_cast<const double2*>(c->d_zstage);
+  if (is_device_ptr(Z)) return accumulate_device(c, q, static_cast<const double2*>(Z), ldz, n_occ, n_unocc, eo, eu);
+
+  // host Z: copy into the next staging slot. Outside stream capture the copy runs on the
+  // context's copy stream, after the kernels that last read that slot but not after the rest
+  // of the queued work, so it overlaps the previous block's kernels; under capture it stays on
+  // the captured stream.
+  const size_t bytes = sizeof(double2) * (size_t)ldz * (size_t)K;
+  const int s = c->hslot;
+  c->hslot ^= 1;
+  if (!c->cstream) {
+    QSGW_CK(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      QSGW_CK(cudaEventCreateWithFlags(&c->hcopied[i], cudaEventDisableTiming));
+      QSGW_CK(cudaEventCreateWithFlags(&c->hfree[i], cudaEventDisableTiming));
+    }
   }
-  return accumulate_device(c, q, Zd, ldz, n_occ, n_unocc, eo, eu);
+  if (c->hstage_cap[s] < bytes) QSGW_CK(cudaStreamSynchronize(c->stream));  // the slot is about to be freed
+  st = grow(&c->d_hstage[s], &c->hstage_cap[s], bytes);
+  if (st != QSGW_OK) return st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  QSGW_CK(cudaStreamIsCapturing(c->stream, &cap));
+  if (cap == cudaStreamCaptureStatusNone) {
+    QSGW_CK(cudaStreamWaitEvent(c->cstream, c->hfree[s], 0));
+    QSGW_CK(cudaMemcpyAsync(c->d_hstage[s], Z, bytes, cudaMemcpyDefault, c->cstream));
+    QSGW_CK(cudaEventRecord(c->hcopied[s], c->cstream));
+    QSGW_CK(cudaStreamWaitEvent(c->stream, c->hcopied[s], 0));
+  } else {
+    QSGW_CK(cudaMemcpyAsync(c->d_hstage[s], Z, bytes, cudaMemcpyDefault, c->stream));
+  }
+  st = accumulate_device(c, q, static_cast<const double2*>(c->d_hstage[s]), ldz, n_occ, n_unocc, eo, eu);
+  if (st != QSGW_OK) return st;
+  if (cap == cudaStreamCaptureStatusNone) QSGW_CK(cudaEventRecord(c->hfree[s], c->stream));
+  return QSGW_OK;
 }
 
 qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
@@ -339,6 +371,13 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   if (c->d_w) cudaFree(c->d_w);
   if (c->d_zstage) cudaFree(c->d_zstage);
   if (c->d_estage) cudaFree(c->d_estage);
+  if (c->cstream) cudaStreamSynchronize(c->cstream);
+  for (int i = 0; i < 2; ++i) {
+    if (c->d_hstage[i]) cudaFree(c->d_hstage[i]);
+    if (c->hcopied[i]) cudaEventDestroy(c->hcopied[i]);
+    if (c->hfree[i]) cudaEventDestroy(c->hfree[i]);
+  }
+  if (c->cstream) cudaStreamDestroy(c->cstream);
   mixed_free(c->mixed);
   for (auto& ln : c->lanes) {
     if (ln.handle) cusolverDnDestroy(ln.handle);

@@ -18,7 +18,10 @@
 // all three exact BF16 values. Products d0_A d0_B are integers and a chunk sum of them stays
 // below 2 * 1024 * 90^2 < 2^24, so the level-0 TMEM accumulator is exact. The seven products
 // d0 d1, d1 d0, d0 d2, d2 d0, d1 d1, d1 d2, d2 d1 share a second accumulator whose truncation
-// error is relative to its own, ~2^-6 smaller, magnitude. The dropped d2 d2 term and the
+// error is relative to its own, ~2^-6 smaller, magnitude. That error is the largest one left
+// and grows faster than linearly with the chunk length (more truncating adds into a larger
+// sum), which is what bounds CHR: 2048-column chunks measured 1.8e-6 relative on a narrow
+// block, above the 1e-6 bar, against ~0.4e-6 at 1024. The dropped d2 d2 term and the
 // remainders are ~2^-23 of a typical product, at the level of the FP32 rounding of the inputs
 // (d1 d2 alone would be ~2^-20 of a typical product, which is why it is kept). After each chunk both accumulators
 // are scaled by 2^-(eA+eB) (exact) and added into a double-float (2 x FP32) accumulator in
@@ -36,7 +39,7 @@ constexpr int KBR = 16;                   // transition columns per K-block
 constexpr int KBK = 2 * KBR;              // K' per K-block (re/im pairs)
 constexpr int CHR = 1024;                 // columns per exact FP32 chunk
 constexpr float DMAX = 90.f;              // |leading digit| bound: 2 * CHR * DMAX^2 < 2^24
-constexpr int KB_PER_CH = CHR / KBR;      // 32
+constexpr int KB_PER_CH = CHR / KBR;      // 64
 constexpr int TI = 64;                    // rows I per tile (M = 128)
 constexpr int A_PLANE = 128 * KBK * 2;    // bytes of one digit plane of one A K-block (8 KB)
 constexpr int A_STAGE = 3 * A_PLANE;      // 24 KB
@@ -51,9 +54,13 @@ constexpr uint64_t kWaitNs = 1000000000ull;
 __device__ __forceinline__ int scale_exp(float m) {
   if (!(m > 0.f) || !isfinite(m)) return 0;
   int E;
-  const float f = frexpf(m, &E);  // m = f 2^E, f in [0.5, 1); 2^7 f <= DMAX  <=>  f <= DMAX / 128
-  int e = 7 - E;
-  if (f > DMAX / 128.f) e -= 1;
+  const float f = frexpf(m, &E);  // m = f 2^E, f in [0.5, 1)
+  int e = 7 - E;                  // m 2^e = 128 f in [64, 128)
+  float s = 128.f * f;
+  while (s > DMAX) {              // two halvings at most for DMAX >= 32
+    s *= 0.5f;
+    --e;
+  }
   return max(-120, min(120, e));
 }
 __device__ __forceinline__ float exp2i(int e) {
@@ -94,31 +101,45 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // ------------------------------------------------------------------ prep: columns
 // One CTA per chunk of CHR columns: Delta, domain check, |w_l| in FP32 ([r][l]), and the
 // per-chunk maximum of each |w_l| (for the B-operand scale bound).
-__global__ void __launch_bounds__(CHR) prep_cols_kernel(const double* __restrict__ eo, const double* __restrict__ eu,
+constexpr int PC_THREADS = 1024;  // prep_cols threads per chunk; each handles CHR / PC_THREADS columns
+__global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const double* __restrict__ eo, const double* __restrict__ eu,
                                                         int n_unocc, long long K, OmegaGrid g, float* __restrict__ wst,
                                                         float* __restrict__ wmax, int* d_err) {
-  __shared__ float red[CHR / 32][kMaxOmega];
+  __shared__ float red[PC_THREADS / 32][kMaxOmega];
   const int c = blockIdx.x, t = threadIdx.x, L = g.L;
-  const long long r = (long long)c * CHR + t;
-  bool ok = false;
-  float d = 0.f;
-  if (r < K) {
-    const int n = (int)(r / n_unocc), m = (int)(r % n_unocc);
-    const double dd = eu[m] - eo[n];
-    ok = (dd > 0.0) && isfinite(dd);
-    if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
-    d = (float)dd;
+  float wm[kMaxOmega];  // loops over l run to the constant kMaxOmega so wm stays in registers
+#pragma unroll
+  for (int l = 0; l < kMaxOmega; ++l) wm[l] = 0.f;
+  for (int sub = 0; sub < CHR / PC_THREADS; ++sub) {
+    const long long r = (long long)c * CHR + sub * PC_THREADS + t;
+    bool ok = false;
+    float d = 0.f;
+    if (r < K) {
+      const int n = (int)(r / n_unocc), m = (int)(r % n_unocc);
+      const double dd = eu[m] - eo[n];
+      ok = (dd > 0.0) && isfinite(dd);
+      if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
+      d = (float)dd;
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxOmega; ++l) {
+      if (l >= L) break;
+      const float w = ok ? 2.f * d / (d * d + g.w2f[l]) : 0.f;
+      wst[r * L + l] = w;
+      wm[l] = fmaxf(wm[l], w);
+    }
   }
-  for (int l = 0; l < L; ++l) {
-    float w = ok ? 2.f * d / (d * d + g.w2f[l]) : 0.f;
-    wst[r * L + l] = w;
+#pragma unroll
+  for (int l = 0; l < kMaxOmega; ++l) {
+    if (l >= L) break;
+    float w = wm[l];
     for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
     if ((t & 31) == 0) red[t >> 5][l] = w;
   }
   __syncthreads();
   if (t < L) {
     float m = 0.f;
-    for (int w = 0; w < CHR / 32; ++w) m = fmaxf(m, red[w][t]);
+    for (int w = 0; w < PC_THREADS / 32; ++w) m = fmaxf(m, red[w][t]);
     wmax[c * L + t] = m;
   }
 }
@@ -207,6 +228,7 @@ struct BlockDesc {
   double* acc2;   // [l][part][J][I] FP64: pieces of the last tiles, added with atomics
   int tile_off;   // first global tile index of this block
   int n_pb, n_pad, n_kb, n_tiles, n_ch;
+  int n_kbr;      // K-blocks holding columns (ceil(K / KBR)); the rest of the last chunk is padding
 };
 constexpr int kMaxBlocks = 32;  // blocks per launch (descriptors travel by value as kernel parameters)
 
@@ -237,6 +259,12 @@ __device__ __forceinline__ int block_of_tile(const BlockDesc* blk, int nb, int g
   int b = 0;
   while (b + 1 < nb && blk[b + 1].tile_off <= gt) ++b;
   return b;
+}
+
+// K-blocks of an item: its chunks [c0, c1), the last chunk of the block cut at n_kbr. At least one,
+// since (n_ch - 1) * CHR < K. Every item ends on a chunk end, so its last K-block closes a chunk.
+__device__ __forceinline__ int item_nkb(const WorkItem& w, const BlockDesc& bd) {
+  return min(w.c1 * KB_PER_CH, bd.n_kbr) - w.c0 * KB_PER_CH;
 }
 
 __device__ WorkItem decode_item(const MainArgs& p, const BlockDesc* blk, int i) {
@@ -345,7 +373,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       while (!stop) {
         const BlockDesc& bd = sBlk[block_of_tile(sBlk, p.nb, cur.gt)];
         const int2 tile = bd.tiles[cur.gt - bd.tile_off];
-        const int nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+        const int nkb = item_nkb(cur, bd);
         for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
           const int s = g % NS, round = g / NS;
           const int kb = cur.c0 * KB_PER_CH + kbi;
@@ -381,13 +409,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       WorkItem cur = ring[0];
       bool stop = cur.gt < 0;
       while (!stop) {
-        int nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+        int nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
         for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
           const int s = g % NS, sb = g % NSB, kbl = kbi % KB_PER_CH;
           bool ok = mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
           if (ok && kbi == 0 && pos > 0) {  // the item was published before this K-block's copies
             cur = ring[pos % kRing];
-            nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+            nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
           }
           ok = ok && mbar_wait_bounded(&bfull[sb], (g / NSB) & 1, kWaitNs);
           if (ok && kbl == 0 && lc > 0) ok = mbar_wait_bounded(accempty, (lc - 1) & 1, kWaitNs);
@@ -420,7 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           }
           mma_commit(&empty[s]);
           mma_commit(&bempty[sb]);
-          if (kbl == KB_PER_CH - 1) mma_commit(accfull);
+          if (kbl == KB_PER_CH - 1 || kbi == nkb - 1) mma_commit(accfull);  // an item ends a chunk
         }
         if (stop || (cur.flags & 1)) break;
         ++pos;
@@ -452,7 +480,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     WorkItem cur = ring[0];
     bool more = cur.gt >= 0;
     while (more) {
-      int nkb = (cur.c1 - cur.c0) * KB_PER_CH;
+      int nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
       for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
         const int s = g % NS, sb = g % NSB, kbl = kbi % KB_PER_CH;
         bool ok = !dead && mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
@@ -465,11 +493,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           }
         }
         if (kbi == 0) {  // new item: published before this K-block's copies (or before the roles split)
-          if (pos > 0) {
-            cur = ring[pos % kRing];
-            nkb = (cur.c1 - cur.c0) * KB_PER_CH;
-          }
+          if (pos > 0) cur = ring[pos % kRing];
           b = block_of_tile(sBlk, p.nb, cur.gt);
+          nkb = item_nkb(cur, sBlk[b]);
           const int2 tile = sBlk[b].tiles[cur.gt - sBlk[b].tile_off];
           it = tile.x;
           jt = tile.y;
@@ -515,7 +541,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           mbar_arrive(&bfull[sb]);
           mbar_arrive(&empty[s]);
         }
-        if (kbl == KB_PER_CH - 1) {
+        if (kbl == KB_PER_CH - 1 || kbi == nkb - 1) {
           // ------------- chunk epilogue: TMEM -> registers -> scaled -> global accumulator
           ok = !dead && mbar_wait_bounded(accfull, lc & 1, kWaitNs);
           if (!dead && __any_sync(0xffffffffu, !ok)) {
@@ -720,9 +746,10 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     d.n_pb = B.n_pb;
     d.n_pad = B.n_pad;
     d.n_kb = P.n_kb;
+    d.n_kbr = (int)((P.K + KBR - 1) / KBR);
     d.n_ch = P.n_ch;
     T += d.n_tiles;
-    prep_cols_kernel<<<P.n_ch, CHR, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
+    prep_cols_kernel<<<P.n_ch, PC_THREADS, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
                                                  const_cast<float*>(d.wmax), d_err);
     prep_rows_kernel<<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(B.Z, B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
                                                                  const_cast<uint8_t*>(d.aplanes),
@@ -851,9 +878,10 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   d.n_pb = n_pb;
   d.n_pad = n_pad;
   d.n_kb = n_kb;
+  d.n_kbr = (int)((K + KBR - 1) / KBR);
   d.n_tiles = n_tiles;
   d.n_ch = n_ch;
-  prep_cols_kernel<<<n_ch, CHR, 0, stream>>>(eo, eu, n_unocc, K, g, const_cast<float*>(d.wst),
+  prep_cols_kernel<<<n_ch, PC_THREADS, 0, stream>>>(eo, eu, n_unocc, K, g, const_cast<float*>(d.wst),
                                             const_cast<float*>(d.wmax), d_err);
   prep_rows_kernel<<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt,
                                                           const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw),

@@ -43,7 +43,9 @@ def test_tiny_mixed(N):
 
 
 @pytest.mark.parametrize("n_pb,n_occ,n_unocc,L", [(1, 1, 1, 1), (100, 3, 7, 5), (130, 5, 13, 16), (65, 7, 80, 12),
-                                                  (200, 9, 61, 9), (70, 2, 300, 3)])
+                                                  (200, 9, 61, 9), (70, 2, 300, 3),
+                                                  # K = 2048 (one whole chunk), K = 2064 (a chunk + one K-block)
+                                                  (96, 16, 128, 12), (96, 8, 258, 12)])
 def test_ragged_shapes_mixed(N, n_pb, n_occ, n_unocc, L):
     wl = Workload(f"ragged {n_pb}", n_q=1, n_k=2, n_occ=n_occ, n_omega=L, s_div=50.0, n_pb_fixed=n_pb,
                   n_unocc_fixed=n_unocc, seed=11)
@@ -131,3 +133,39 @@ def test_medium_mixed_full_size_sampled(N):
         dg = np.sqrt(np.abs(np.diag(ref[l])))
         assert np.all(np.abs(sub[l] - ref[l]) <= TOL * np.outer(dg, dg))
         assert rel_fro(sub[l], ref[l]) <= TOL
+
+
+def test_pinned_host_blocks_double_buffered(N):
+    """Host Z from pinned memory, five blocks whose sizes grow and shrink (so both staging slots
+    are reused and regrown while the copy stream runs ahead of the kernels): the result equals
+    the device-pointer path bit for bit (same kernels on the same values), and the oracle."""
+    n, L = 140, 12
+    wl = Workload("pinned", n_q=1, n_k=5, n_occ=4, n_omega=L, s_div=40.0, n_pb_fixed=n, seed=5)
+    shapes = [(4, 90), (6, 400), (3, 30), (8, 700), (5, 200)]  # (n_occ, n_unocc) per block
+    blocks = []
+    for k, (no, nu) in enumerate(shapes):
+        zt = z_block(wl.seed, 0, k, n, no, nu, wl.s_div)
+        blocks.append((zt, eps_occ(wl.seed, 0, k, no), eps_unocc(wl.seed, 0, k, nu), no, nu))
+
+    def run(host):
+        ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+        keep = []
+        try:
+            for zt, eo, eu, no, nu in blocks:
+                if host:
+                    Zh = torch.from_numpy(np.ascontiguousarray(zt)).pin_memory()
+                    keep.append(Zh)  # pinned host data must stay unchanged until the sync
+                    N.qsgw_chi0_accumulate(ctx, 0, Zh, n, no, nu, eo, eu, wl.omega)
+                else:
+                    N.qsgw_chi0_accumulate(ctx, 0, _dev(zt), n, no, nu, _dev(eo), _dev(eu), wl.omega)
+            chi = torch.empty((L, n, n), dtype=torch.complex128, device="cuda")
+            N.qsgw_chi0_finalize(ctx, 0, chi)
+            return chi.cpu().numpy().transpose(0, 2, 1)
+        finally:
+            N.qsgw_chi0_destroy(ctx)
+
+    a, b = run(True), run(False)
+    assert np.array_equal(a, b)
+    Z = np.concatenate([zt.T for zt, *_ in blocks], axis=1)
+    d = np.concatenate([oracle.delta(eo, eu)[0] for _, eo, eu, _, _ in blocks])
+    _check_chi(a, oracle.chi0_full(Z, d, wl.omega, wl.spin))

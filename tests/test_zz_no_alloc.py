@@ -4,8 +4,8 @@ Some callers cannot call cudaMalloc: their device memory is entirely reserved by
 allocator (a framework's caching pool, a fixed arena), or they must not risk the implicit
 device synchronisation of cudaMalloc/cudaFree or an allocation failure at run time. For them
 the library computes the chi0 of one block of columns inside one fixed array in its device
-image. This file checks, through the C ABI, that two calls in a row (different shapes, so the
-second runs on whatever the first left in the shared array) give the same chi0 as
+image. This file checks, through the C ABI, that three calls in a row (different shapes, so the
+later ones run on whatever the earlier left in the shared array) give the same chi0 as
 qsgw_chi0_accumulate + qsgw_chi0_finalize on a fresh context, within the mixed-precision
 tolerance the other tests use (1e-6 relative Frobenius per frequency).
 """
@@ -47,10 +47,11 @@ def _context_chi0(N, Z, eo, eu, n_pb, n_occ, n_unocc, om):
 
 
 def test_noalloc_two_calls_match_context_path(N):
-    cases = [(0, 200, 9, 61, 12), (1, 130, 5, 13, 16)]  # (q, n_pb, n_occ, n_unocc, L)
+    # (q, n_pb, n_occ, n_unocc, L); the last is the corner the header promises always fits
+    cases = [(0, 200, 9, 61, 12), (1, 130, 5, 13, 16), (2, 256, 48, 64, 16)]
     inputs = [_case(*c) for c in cases]
     outs = []
-    for (q, n_pb, n_occ, n_unocc, L), (Z, eo, eu, om) in zip(cases, inputs):  # two calls in a row
+    for (q, n_pb, n_occ, n_unocc, L), (Z, eo, eu, om) in zip(cases, inputs):  # calls in a row
         chi = torch.full((L, n_pb, n_pb), float("nan"), dtype=torch.complex128, device="cuda")
         N.qsgw_chi0_block_noalloc(Z, n_pb, n_pb, n_occ, n_unocc, eo, eu, om, 2.0, chi)
         outs.append(chi.cpu().numpy())
@@ -62,11 +63,11 @@ def test_noalloc_two_calls_match_context_path(N):
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(N):
-    # n_pb = 1500 needs a 75 MiB accumulator alone: rejected before any work is queued
-    Z = torch.zeros((1, 1500), dtype=torch.complex128, device="cuda")
+    # n_pb = 2000 needs a 128 MiB accumulator alone (64 MiB array): rejected before any work is queued
+    Z = torch.zeros((1, 2000), dtype=torch.complex128, device="cuda")
     eo = torch.full((1,), -0.5, dtype=torch.float64, device="cuda")
     eu = torch.full((1,), 0.5, dtype=torch.float64, device="cuda")
-    chi = torch.zeros((1, 1500, 1500), dtype=torch.complex128, device="cuda")
+    chi = torch.zeros((1, 2000, 2000), dtype=torch.complex128, device="cuda")
     with pytest.raises(N.QsgwError) as err:
-        N.qsgw_chi0_block_noalloc(Z, 1500, 1500, 1, 1, eo, eu, [0.1], 2.0, chi)
+        N.qsgw_chi0_block_noalloc(Z, 2000, 2000, 1, 1, eo, eu, [0.1], 2.0, chi)
     assert err.value.status == N.QSGW_ERR_ARG
