@@ -40,8 +40,8 @@ CONFIG_NAME = "medium chi0+W: n_pb=1500, n_k=64, n_occ=40, n_unocc=400 (K=1,024,
 # DRAM traffic of one herk_mixed_kernel launch of this workload (one k-point), from the ncu
 # capture summarised in profiles/herk_mixed_kernel_medium_one_kpoint.md; valid only for the kernel
 # source it was measured on (sha1 prefix), otherwise reported as null.
-TRAFFIC_BYTES_PER_LAUNCH = 2.853e9
-TRAFFIC_KERNEL_SHA1 = "85e0b59e4e6d"
+TRAFFIC_BYTES_PER_LAUNCH = 9.306e9
+TRAFFIC_KERNEL_SHA1 = "bf1e139d3f0b"
 
 
 def measured_traffic():
@@ -223,6 +223,18 @@ def run_ours(args, rank, world, dev_index):
             stream.synchronize()
 
         e2e_step()
+        # the box's own pinned host-to-device rate on one k-point slab (context for the e2e figure:
+        # the 24.6 GB per step cross the host link once, overlapped with the kernels)
+        probe = torch.empty(Zh[0].shape, dtype=Zh.dtype, device=dev)
+        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            pa.record(stream)
+            for _ in range(4):
+                probe.copy_(Zh[0], non_blocking=True)
+            pb.record(stream)
+        stream.synchronize()
+        h2d_gbs = 4 * Zh[0].numel() * 16 / (pa.elapsed_time(pb) * 1e-3) / 1e9
+        del probe
         barrier(world)
         t = time.perf_counter()
         n_e2e = max(1, min(args.steps, 3))
@@ -233,7 +245,7 @@ def run_ours(args, rank, world, dev_index):
         h2d = Zh.numel() * 16 + (eoh.size + euh.size) * 8
         d2h = 2 * chi.numel() * 16
         e2e = {"value": world * F_STEP * nk / N_K / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3, "h2d_gbs_measured": h2d_gbs}
     N.qsgw_chi0_destroy(ctx)
 
     res = dict(ms_step=ms_step, acc_ms=acc_ms, fp64=fp64, e2e=e2e, clocks=clk.summary(),

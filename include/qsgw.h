@@ -84,12 +84,13 @@ qsgw_status qsgw_chi0_init(qsgw_ctx **ctx, int n_q, const int *n_pb, int n_omega
  *   n_omega, omega  must equal the grid given to qsgw_chi0_init (host), else QSGW_ERR_ARG
  * Columns with Delta <= 0 or non-finite contribute nothing and set QSGW_ERR_DOMAIN (sticky).
  * The result does not depend on how columns are split across calls, up to rounding.
- * A host Z is copied into one of two device staging buffers the context owns (allocated on
- * first use, grown when a larger block arrives). Outside stream capture the copy runs on an
- * internal copy stream, so it overlaps the kernels of the previous call; it is NOT ordered
- * after earlier work queued on cuda_stream, so the host array must hold its data when the
- * call is made, and (pinned memory) stay unchanged until qsgw_chi0_sync or qsgw_chi0_finalize.
- * Host eps arrays are copied in stream order. */
+ * Host arrays are copied into one of two device staging slots the context owns (allocated on
+ * first use, grown when a larger block arrives). Outside stream capture the copies run on an
+ * internal copy stream, so they overlap the kernels of the previous call; they are NOT
+ * ordered after earlier work queued on cuda_stream, so host arrays must hold their data when
+ * the call is made. Host eps arrays are read during the call (through a pinned buffer of the
+ * context); a host Z in pinned memory must stay unchanged until qsgw_chi0_sync or
+ * qsgw_chi0_finalize, one in pageable memory is read before the call returns. */
 qsgw_status qsgw_chi0_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_unocc,
                                  const double *eps_occ, const double *eps_unocc, int n_omega, const double *omega);
 

@@ -44,12 +44,14 @@ struct qsgw_ctx {
   size_t w_cap = 0;  // doubles
   void* d_zstage = nullptr;
   size_t zstage_cap = 0;  // bytes
-  double* d_estage = nullptr;
-  size_t estage_cap = 0;  // doubles
-  // host Z: two device staging slots filled on a copy stream, so the copy of one block
-  // overlaps the kernels of the previous one
-  void* d_hstage[2] = {};
+  // host operands: two staging slots filled on a copy stream, so the copies of one block
+  // overlap the kernels of the previous one
+  void* d_hstage[2] = {};     // Z
   size_t hstage_cap[2] = {};  // bytes
+  double* d_es[2] = {};       // eps_occ, eps_unocc
+  size_t es_cap[2] = {};      // bytes
+  double* h_eb[2] = {};       // pinned bounce buffers for host eps
+  size_t eb_cap[2] = {};      // bytes
   cudaStream_t cstream = nullptr;
   cudaEvent_t hcopied[2] = {};  // slot filled (recorded on cstream)
   cudaEvent_t hfree[2] = {};    // last reader of the slot done (recorded on stream)
@@ -89,6 +91,21 @@ qsgw_status grow(void** p, size_t* cap, size_t need_bytes) {
   *p = nullptr;
   *cap = 0;
   QSGW_CK(cudaMalloc(p, need_bytes));
+  *cap = need_bytes;
+  return QSGW_OK;
+}
+
+// Pinned host buffer of at least need_bytes (the caller has made sure no copy still reads it).
+qsgw_status grow_pinned(void** p, size_t* cap, size_t need_bytes) {
+  if (*cap >= need_bytes) return QSGW_OK;
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMallocHost(p, need_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return QSGW_ERR_NOMEM;
+  }
   *cap = need_bytes;
   return QSGW_OK;
 }
@@ -207,25 +224,20 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ld
   if (st != QSGW_OK) return st;
   const long long K = (long long)n_occ * n_unocc;
 
-  const double* eo = eps_occ;
-  const double* eu = eps_unocc;
-  if (!is_device_ptr(eps_occ) || !is_device_ptr(eps_unocc)) {
-    st = grow(reinterpret_cast<void**>(&c->d_estage), &c->estage_cap, sizeof(double) * (size_t)(n_occ + n_unocc));
-    if (st != QSGW_OK) return st;
-    QSGW_CK(cudaMemcpyAsync(c->d_estage, eps_occ, sizeof(double) * n_occ, cudaMemcpyDefault, c->stream));
-    QSGW_CK(cudaMemcpyAsync(c->d_estage + n_occ, eps_unocc, sizeof(double) * n_unocc, cudaMemcpyDefault, c->stream));
-    eo = c->d_estage;
-    eu = c->d_estage + n_occ;
-  }
-  if (is_device_ptr(Z)) return accumulate_device(c, q, static_cast<const double2*>(Z), ldz, n_occ, n_unocc, eo, eu);
+  const bool z_dev = is_device_ptr(Z);
+  const bool e_dev = is_device_ptr(eps_occ) && is_device_ptr(eps_unocc);
+  if (z_dev && e_dev)
+    return accumulate_device(c, q, static_cast<const double2*>(Z), ldz, n_occ, n_unocc, eps_occ, eps_unocc);
 
-  // host Z: copy into the next staging slot. Outside stream capture the copy runs on the
-  // context's copy stream, after the kernels that last read that slot but not after the rest
-  // of the queued work, so it overlaps the previous block's kernels; under capture it stays on
-  // the captured stream.
-  const size_t bytes = sizeof(double2) * (size_t)ldz * (size_t)K;
-  const int s = c->hslot;
-  c->hslot ^= 1;
+  // Host operands go through the next of two staging slots. Outside stream capture their copies
+  // run on the context's copy stream, after the kernels that last read that slot but not after
+  // the rest of the queued work, so they overlap the previous call's kernels. Host eps pass
+  // through a pinned bounce buffer, so no copy from pageable memory is queued (such a copy may
+  // hold the caller until the stream reaches it, which would serialise the calls). Under stream
+  // capture the copies stay on the captured stream and read the caller's arrays directly.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  QSGW_CK(cudaStreamIsCapturing(c->stream, &cap));
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
   if (!c->cstream) {
     QSGW_CK(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) {
@@ -233,22 +245,50 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ld
       QSGW_CK(cudaEventCreateWithFlags(&c->hfree[i], cudaEventDisableTiming));
     }
   }
-  if (c->hstage_cap[s] < bytes) QSGW_CK(cudaStreamSynchronize(c->stream));  // the slot is about to be freed
-  st = grow(&c->d_hstage[s], &c->hstage_cap[s], bytes);
-  if (st != QSGW_OK) return st;
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  QSGW_CK(cudaStreamIsCapturing(c->stream, &cap));
-  if (cap == cudaStreamCaptureStatusNone) {
-    QSGW_CK(cudaStreamWaitEvent(c->cstream, c->hfree[s], 0));
-    QSGW_CK(cudaMemcpyAsync(c->d_hstage[s], Z, bytes, cudaMemcpyDefault, c->cstream));
-    QSGW_CK(cudaEventRecord(c->hcopied[s], c->cstream));
-    QSGW_CK(cudaStreamWaitEvent(c->stream, c->hcopied[s], 0));
-  } else {
-    QSGW_CK(cudaMemcpyAsync(c->d_hstage[s], Z, bytes, cudaMemcpyDefault, c->stream));
+  const int s = c->hslot;
+  c->hslot ^= 1;
+  const size_t zbytes = z_dev ? 0 : sizeof(double2) * (size_t)ldz * (size_t)K;
+  const size_t ebytes = e_dev ? 0 : sizeof(double) * (size_t)(n_occ + n_unocc);
+  if (c->hstage_cap[s] < zbytes || c->es_cap[s] < ebytes || c->eb_cap[s] < ebytes) {
+    // the slot is about to be reallocated: nothing may still fill or read it
+    QSGW_CK(cudaStreamSynchronize(c->cstream));
+    QSGW_CK(cudaStreamSynchronize(c->stream));
   }
-  st = accumulate_device(c, q, static_cast<const double2*>(c->d_hstage[s]), ldz, n_occ, n_unocc, eo, eu);
+  st = grow(&c->d_hstage[s], &c->hstage_cap[s], zbytes);
+  if (st == QSGW_OK) st = grow(reinterpret_cast<void**>(&c->d_es[s]), &c->es_cap[s], ebytes);
+  if (st == QSGW_OK) st = grow_pinned(reinterpret_cast<void**>(&c->h_eb[s]), &c->eb_cap[s], ebytes);
   if (st != QSGW_OK) return st;
-  if (cap == cudaStreamCaptureStatusNone) QSGW_CK(cudaEventRecord(c->hfree[s], c->stream));
+
+  cudaStream_t cs = capturing ? c->stream : c->cstream;
+  if (!capturing) QSGW_CK(cudaStreamWaitEvent(cs, c->hfree[s], 0));
+  const double* eo = eps_occ;
+  const double* eu = eps_unocc;
+  if (!e_dev) {
+    const size_t bo = sizeof(double) * (size_t)n_occ, bu = sizeof(double) * (size_t)n_unocc;
+    if (!capturing) {
+      QSGW_CK(cudaEventSynchronize(c->hcopied[s]));  // the bounce buffer's previous copy is done
+      std::memcpy(c->h_eb[s], eps_occ, bo);
+      std::memcpy(c->h_eb[s] + n_occ, eps_unocc, bu);
+      QSGW_CK(cudaMemcpyAsync(c->d_es[s], c->h_eb[s], ebytes, cudaMemcpyHostToDevice, cs));
+    } else {
+      QSGW_CK(cudaMemcpyAsync(c->d_es[s], eps_occ, bo, cudaMemcpyDefault, cs));
+      QSGW_CK(cudaMemcpyAsync(c->d_es[s] + n_occ, eps_unocc, bu, cudaMemcpyDefault, cs));
+    }
+    eo = c->d_es[s];
+    eu = c->d_es[s] + n_occ;
+  }
+  const double2* Zd = static_cast<const double2*>(Z);
+  if (!z_dev) {
+    QSGW_CK(cudaMemcpyAsync(c->d_hstage[s], Z, zbytes, cudaMemcpyDefault, cs));
+    Zd = static_cast<const double2*>(c->d_hstage[s]);
+  }
+  if (!capturing) {
+    QSGW_CK(cudaEventRecord(c->hcopied[s], cs));
+    QSGW_CK(cudaStreamWaitEvent(c->stream, c->hcopied[s], 0));
+  }
+  st = accumulate_device(c, q, Zd, ldz, n_occ, n_unocc, eo, eu);
+  if (st != QSGW_OK) return st;
+  if (!capturing) QSGW_CK(cudaEventRecord(c->hfree[s], c->stream));
   return QSGW_OK;
 }
 
@@ -370,10 +410,11 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
     if (a.acc) cudaFree(a.acc);
   if (c->d_w) cudaFree(c->d_w);
   if (c->d_zstage) cudaFree(c->d_zstage);
-  if (c->d_estage) cudaFree(c->d_estage);
   if (c->cstream) cudaStreamSynchronize(c->cstream);
   for (int i = 0; i < 2; ++i) {
     if (c->d_hstage[i]) cudaFree(c->d_hstage[i]);
+    if (c->d_es[i]) cudaFree(c->d_es[i]);
+    if (c->h_eb[i]) cudaFreeHost(c->h_eb[i]);
     if (c->hcopied[i]) cudaEventDestroy(c->hcopied[i]);
     if (c->hfree[i]) cudaEventDestroy(c->hfree[i]);
   }

@@ -46,7 +46,8 @@ constexpr int A_STAGE = 3 * A_PLANE;      // 24 KB
 constexpr int NS = 4;                     // load pipeline stages
 constexpr int NSB = 2;                    // B operand stages
 constexpr int NBG = 256;                  // B-operand / epilogue threads (warps 2..9)
-constexpr int NTHREADS = 64 + NBG;
+constexpr int NDR = 64;                   // drainer threads (warps 10, 11): deferred accumulator updates
+constexpr int NTHREADS = 64 + NBG + NDR;
 constexpr uint32_t TMEM_L12 = 256;        // column of the level-1+2 accumulator
 constexpr uint64_t kWaitNs = 1000000000ull;
 
@@ -231,6 +232,7 @@ struct BlockDesc {
   int n_kbr;      // K-blocks holding columns (ceil(K / KBR)); the rest of the last chunk is padding
 };
 constexpr int kMaxBlocks = 32;  // blocks per launch (descriptors travel by value as kernel parameters)
+constexpr int kFscrPerCta = 256 * 128;  // flush scratch pairs per CTA: [column n < 256][accumulator lane < 128]
 
 // Work schedule. The T tiles of all blocks (block-major, then tile-major, so consecutive tiles share
 // their row operand) are handed out whole through a global counter, so the CTAs run through them in
@@ -246,6 +248,7 @@ struct MainArgs {
   int L, TJ, N;
   uint32_t idesc;
   int* d_err;
+  float2* fscr;  // per-CTA flush scratch, kFscrPerCta pairs each (see the chunk epilogue)
 };
 
 struct WorkItem {
@@ -304,6 +307,8 @@ __host__ __device__ constexpr size_t main_smem_bytes(int N, int TJ, int L) {
          sizeof(WorkItem) * kRing;
 }
 
+// 168 registers at most: the register file is split over the 4 SM sub-partitions and 10 warps
+// put 3 on some of them (3 * 32 * 168 <= 16384); __launch_bounds__ lets ptxas enforce it.
 __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -324,8 +329,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint64_t* accfull = bempty + NSB;  // MMA commit at chunk end -> epilogue
   uint64_t* accempty = accfull + 1;  // 8 epilogue warps -> MMA
   uint64_t* finbar = accempty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(finbar + 1);
+  uint64_t* stashed = finbar + 1;    // 8 epilogue warps -> drainers: a chunk end (stash or heartbeat)
+  uint64_t* drained = stashed + 1;   // 2 drainer warps -> epilogue: that stash is in the accumulator
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
   int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [2] builder-warp failure flags, by chunk parity
+  int* sdesc = abortB + 2;  // [4] stash descriptor: kind (0 nothing, 1 whole-tile chunk, 2 end), block, it, jt
   BlockDesc* sBlk = reinterpret_cast<BlockDesc*>(bars + 32);  // block table, copied from the parameters
   WorkItem* ring = reinterpret_cast<WorkItem*>(sBlk + kMaxBlocks);  // items in flight, producer -> others
 
@@ -344,6 +352,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     mbar_init(accfull, 1);
     mbar_init(accempty, NBG / 32);
     mbar_init(finbar, 1);
+    mbar_init(stashed, NBG / 32);
+    mbar_init(drained, NDR / 32);
     abortB[0] = abortB[1] = 0;
     fence_mbar_init();
   }
@@ -457,7 +467,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       mma_commit(finbar);
       mbar_wait_bounded(finbar, 0, kWaitNs);
     }
-  } else {
+  } else if (warp < 2 + NBG / 32) {
     // ---------------- B operand generation (scaled digits, all frequencies) + chunk epilogue
     const int bt = tid - 64;
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
@@ -471,6 +481,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     float bsc = 0.f;
     bool bjok = false;
     int it = 0, jt = 0, b = 0;
+    // Deferred flush. At a chunk end of a whole tile the epilogue stores the two scaled
+    // accumulator levels to this CTA's scratch (plain stores, no loads), frees TMEM and hands the
+    // stash to the drainer warps, which do the double-float read-modify-write of the accumulator
+    // while the next chunk runs. Every chunk end is announced (pieces as an empty stash), so a
+    // drainer never waits longer than one chunk. A warp whose wait on the drainers times out
+    // ("ddead") stops stashing and waiting; the error flag is set.
+    float2* const fscr = p.fscr + (size_t)blockIdx.x * kFscrPerCta;
+    int ns = 0;  // chunk ends announced
+    bool ddead = false;
     // A warp whose wait timed out ("dead", warp-uniform) skips waits and work for the rest of its
     // chunk and sets abortB[chunk parity]; at that chunk's epilogue barrier every builder warp reads
     // the flag and all leave together, so no named barrier is ever left short of a warp. (Items end
@@ -557,6 +576,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             break;
           }
           ++lc;
+          if (ns > 0 && !ddead) {  // the drainers are done with the previous stash: scratch and descriptor free
+            const bool okd = mbar_wait_bounded(drained, (ns - 1) & 1, kWaitNs);
+            if (__any_sync(0xffffffffu, !okd)) {
+              ddead = true;
+              if (lane == 0) atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+            }
+          }
           tc_fence_after();
           const int I = it * TI + (m_row % TI);
           const int eA = bd.expA[(size_t)c * bd.n_pad + I];
@@ -590,37 +616,95 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
               }
               continue;
             }
-            // all global loads of the group first (independent), then the double-float adds and stores
-            float2* accI = bd.acc + base;
-            float2 v[16];
-            uint32_t okc = 0;
+            // whole tile: scale both levels (exact) and stash; the drainers add them to the accumulator
+            if (ddead) continue;
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
-              if (jj < cnt && iok && J < bd.n_pb) {
-                okc |= 1u << jj;
-                v[jj] = accI[(size_t)l * 2 * nn + (size_t)J * bd.n_pad];
-              }
-            }
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              if (okc & (1u << jj)) {
-                const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
+            for (int jj = 0; jj < 16; ++jj)
+              if (jj < cnt) {
+                const int n = col0 + jj;
                 const float sc = exp2i(-(eA + sExpB[n]));
-                df_add(v[jj], __uint_as_float(r0[jj]) * sc);
-                df_add(v[jj], __uint_as_float(r1[jj]) * sc);
-                accI[(size_t)l * 2 * nn + (size_t)J * bd.n_pad] = v[jj];
+                fscr[n * 128 + m_row] = make_float2(__uint_as_float(r0[jj]) * sc, __uint_as_float(r1[jj]) * sc);
               }
-            }
           }
           tc_fence_before();
+          __threadfence_block();  // the stash is visible before it is announced
           __syncwarp();
           if (lane == 0) mbar_arrive(accempty);
+          if (bt == 0) {
+            sdesc[0] = piece ? 0 : 1;
+            sdesc[1] = b;
+            sdesc[2] = it;
+            sdesc[3] = jt;
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(stashed);
+          ++ns;
           named_bar_sync(1, NBG);  // exponent table of this chunk no longer needed
         }
       }
       more = more && !(cur.flags & 1);
       ++pos;
+    }
+    // end of work: let the drainers finish the last stash, then tell them to stop
+    if (ns > 0 && !ddead && !mbar_wait_bounded(drained, (ns - 1) & 1, kWaitNs) && lane == 0)
+      atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+    __syncwarp();
+    if (bt == 0) sdesc[0] = 2;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(stashed);
+  } else {
+    // ---------------- drainers: double-float read-modify-write of each stashed whole-tile chunk.
+    // Thread (warp dw, lane) owns accumulator lanes m = dw * 32 + lane (Re rows) and m + 64 (Im
+    // rows), i.e. row I = it * 64 + m of the tile, for all N columns; 8 columns (16 elements) per
+    // round trip. Each element of a whole tile is written by this CTA only.
+    const int mlo = (warp - 2 - NBG / 32) * 32 + lane;
+    const float2* const fscr = p.fscr + (size_t)blockIdx.x * kFscrPerCta;
+    for (int nd = 0;; ++nd) {
+      if (!mbar_wait_bounded(stashed, nd & 1, kWaitNs)) {
+        if (lane == 0) atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
+        break;
+      }
+      const int kind = sdesc[0];
+      if (kind == 2) break;
+      if (kind == 1) {
+        const BlockDesc& bd = sBlk[sdesc[1]];
+        const int it = sdesc[2], jt = sdesc[3];
+        const int I = it * TI + mlo;
+        if (I < bd.n_pb) {
+          const size_t nn = (size_t)bd.n_pad * bd.n_pad;
+          float2* const acc = bd.acc + I;
+          const int jmax = bd.n_pb - jt * TJ;  // tile columns j < jmax lie inside the matrix
+          for (int n0 = 0; n0 < N; n0 += 8) {
+            float2 x[16], v[16];
+            size_t off[8];
+            uint32_t okm = 0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int n = n0 + e, l = n / TJ, j = n - l * TJ;
+              if (n < N && j < jmax) {
+                okm |= 1u << e;
+                off[e] = (size_t)l * 2 * nn + (size_t)(jt * TJ + j) * bd.n_pad;
+                x[2 * e] = fscr[n * 128 + mlo];
+                x[2 * e + 1] = fscr[n * 128 + mlo + 64];
+                v[2 * e] = acc[off[e]];
+                v[2 * e + 1] = acc[off[e] + nn];
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (okm & (1u << e)) {
+                df_add(v[2 * e], x[2 * e].x);
+                df_add(v[2 * e], x[2 * e].y);
+                df_add(v[2 * e + 1], x[2 * e + 1].x);
+                df_add(v[2 * e + 1], x[2 * e + 1].y);
+                acc[off[e]] = v[2 * e];
+                acc[off[e] + nn] = v[2 * e + 1];
+              }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(drained);
     }
   }
   tc_fence_before();
@@ -676,8 +760,14 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     int n_ch, n_kb, n_it, n_jt;
     size_t o_a, o_raw, o_w, o_zmax, o_exp, o_wmax;
   };
+  if (s.n_sm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return QSGW_ERR_CUDA;
+  }
   std::vector<Plan> pl(nb);
-  size_t total = 0;
+  size_t total = align256((size_t)s.n_sm * kFscrPerCta * sizeof(float2));  // flush scratch first
   for (int b = 0; b < nb; ++b) {
     Plan& P = pl[b];
     const MixedBlock& B = in[b];
@@ -706,12 +796,6 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     if (cudaMalloc(&s.planes, total) != cudaSuccess) return QSGW_ERR_NOMEM;
     s.planes_cap = total;
   }
-  if (s.n_sm == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&s.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return QSGW_ERR_CUDA;
-  }
   if (!s.attr_set) {
     if (cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
         cudaSuccess)
@@ -727,6 +811,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
   a.d_err = d_err;
   uint8_t* base = static_cast<uint8_t*>(s.planes);
+  a.fscr = reinterpret_cast<float2*>(base);
   int T = 0, min_ch_tail = 1 << 30;
   for (int b = 0; b < nb; ++b) {
     const Plan& P = pl[b];
@@ -846,7 +931,10 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   off += align256((size_t)n_ch * n_pad * sizeof(int));
   const size_t o_wmax = off;
   off += align256((size_t)n_ch * L * sizeof(float));
-  if (off > kNoAllocBytes) return QSGW_ERR_ARG;  // beyond the fixed array: use the context API
+  // the rest holds the per-CTA flush scratch; the grid is capped to the CTAs it has room for
+  const size_t o_fscr = off, fscr_cta = (size_t)kFscrPerCta * sizeof(float2);
+  if (off + fscr_cta > kNoAllocBytes) return QSGW_ERR_ARG;  // beyond the fixed array: use the context API
+  const int cap_ctas = (int)((kNoAllocBytes - off) / fscr_cta);
   uint8_t* base = static_cast<uint8_t*>(g_noalloc_ptr[dev]);
   int* d_err = reinterpret_cast<int*>(base);
   int* counter = d_err + 1;
@@ -886,7 +974,8 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   prep_rows_kernel<<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt,
                                                           const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw),
                                                           const_cast<float*>(d.zmax), const_cast<int*>(d.expA));
-  const int G = n_sm, T = n_tiles;
+  a.fscr = reinterpret_cast<float2*>(base + o_fscr);
+  const int G = n_sm < cap_ctas ? n_sm : cap_ctas, T = n_tiles;
   const int R = T >= G ? T % G : T;
   a.T = T;
   a.T_whole = T - R;

@@ -147,15 +147,19 @@ def test_pinned_host_blocks_double_buffered(N):
         zt = z_block(wl.seed, 0, k, n, no, nu, wl.s_div)
         blocks.append((zt, eps_occ(wl.seed, 0, k, no), eps_unocc(wl.seed, 0, k, nu), no, nu))
 
-    def run(host):
+    def run(mode):
         ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
         keep = []
         try:
             for zt, eo, eu, no, nu in blocks:
-                if host:
+                if mode == "pinned":  # pinned Z, pageable eps
                     Zh = torch.from_numpy(np.ascontiguousarray(zt)).pin_memory()
                     keep.append(Zh)  # pinned host data must stay unchanged until the sync
                     N.qsgw_chi0_accumulate(ctx, 0, Zh, n, no, nu, eo, eu, wl.omega)
+                elif mode == "eps_host":  # device Z, pageable eps
+                    Zd = _dev(zt)
+                    keep.append(Zd)
+                    N.qsgw_chi0_accumulate(ctx, 0, Zd, n, no, nu, eo.copy(), eu.copy(), wl.omega)
                 else:
                     N.qsgw_chi0_accumulate(ctx, 0, _dev(zt), n, no, nu, _dev(eo), _dev(eu), wl.omega)
             chi = torch.empty((L, n, n), dtype=torch.complex128, device="cuda")
@@ -164,8 +168,8 @@ def test_pinned_host_blocks_double_buffered(N):
         finally:
             N.qsgw_chi0_destroy(ctx)
 
-    a, b = run(True), run(False)
-    assert np.array_equal(a, b)
+    a, b, c = run("pinned"), run("device"), run("eps_host")
+    assert np.array_equal(a, b) and np.array_equal(c, b)
     Z = np.concatenate([zt.T for zt, *_ in blocks], axis=1)
     d = np.concatenate([oracle.delta(eo, eu)[0] for _, eo, eu, _, _ in blocks])
     _check_chi(a, oracle.chi0_full(Z, d, wl.omega, wl.spin))
