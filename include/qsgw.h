@@ -57,8 +57,13 @@ typedef enum {
 
 typedef enum {
   QSGW_FP64 = 0,        /* FP64 arithmetic end to end (CUDA-core DFMA) */
-  QSGW_MIXED_BF16X3 = 1 /* tcgen05 tensor cores on exact 3-digit BF16 slices, FP32 per chunk,
+  QSGW_MIXED_BF16X3 = 1, /* tcgen05 tensor cores on exact 3-digit BF16 slices, FP32 per chunk,
                            double-float (2 x FP32) across chunks; eps and W stay FP64 */
+  QSGW_MIXED_TF32X3 = 2  /* reserved, rejected by qsgw_chi0_init with QSGW_ERR_ARG: TF32 hi/lo
+                            splitting (3 products) has no exact leading level, and the tensor
+                            cores' truncating FP32 accumulation leaves 4e-6..1.7e-5 relative error,
+                            above the 1e-6 bar; an exact-digit TF32 form needs 6 products at half
+                            the BF16 rate, slower than QSGW_MIXED_BF16X3 */
 } qsgw_prec;
 
 /* Create a context for n_q independent q-points (Alg. 1 loops over q; each q has its own

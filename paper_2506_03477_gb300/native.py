@@ -24,6 +24,7 @@ QSGW_ERR_TIMEOUT = -6
 QSGW_ERR_STATE = -7
 QSGW_FP64 = 0
 QSGW_MIXED_BF16X3 = 1
+QSGW_MIXED_TF32X3 = 2  # reserved: rejected with QSGW_ERR_ARG
 
 EXPORTS = [
     "qsgw_chi0_init", "qsgw_chi0_accumulate", "qsgw_chi0_finalize", "qsgw_eps_inv", "qsgw_chi0_reset",

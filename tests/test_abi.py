@@ -44,3 +44,6 @@ def test_argument_errors_are_synchronous_without_gpu():
     with pytest.raises(native.QsgwError) as e:
         native.qsgw_chi0_init([10], [0.1] * 17, 2.0, native.QSGW_FP64, stream=0)
     assert e.value.status == native.QSGW_ERR_ARG
+    with pytest.raises(native.QsgwError) as e:  # the reserved TF32 form is rejected before any device work
+        native.qsgw_chi0_init([10], [0.1], 2.0, native.QSGW_MIXED_TF32X3, stream=0)
+    assert e.value.status == native.QSGW_ERR_ARG
