@@ -100,6 +100,18 @@ __device__ __forceinline__ void digits3(float t, float& d0, float& d1, float& d2
   d2 = hi8_int(u2);
 }
 
+// Three BF16-exact digits of the exact product a * b (|a b| <= DMAX + 1/2), with the product fused
+// into the rounding: fma(a, b, 1.5 * 2^23) rounds a b to the nearest integer in one step, and
+// u = fma(a, b, -d0) is a b - d0 rounded once (|u| <= 1/2), so d0 + d1 + d2 follows the exact
+// product rather than fl(a b). Three FP32 operations where a product and digits3 take four.
+__device__ __forceinline__ void digits3_mul(float a, float b, float& d0, float& d1, float& d2) {
+  d0 = __fsub_rn(__fmaf_rn(a, b, 12582912.0f), 12582912.0f);
+  const float u = __fmaf_rn(a, b, -d0);
+  d1 = hi8_int(u);
+  const float u2 = __fsub_rn(u, d1);
+  d2 = hi8_int(u2);
+}
+
 // Two BF16-exact FP32 values -> packed bf16x2 (lo in the low half): their upper 16 bits.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
@@ -546,8 +558,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
               const int rl = kg * 4 + rr;
               const float2 z = bjok ? raw[rl * TJ] : make_float2(0.f, 0.f);
               const float ww = ws[rl * L] * bsc;
-              digits3(ww * z.x, d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
-              digits3(ww * z.y, d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
+              digits3_mul(ww, z.x, d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
+              digits3_mul(ww, z.y, d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
             }
 #pragma unroll
             for (int pl = 0; pl < 3; ++pl) {
