@@ -104,12 +104,13 @@ __device__ __forceinline__ void digits3(float t, float& d0, float& d1, float& d2
 // into the rounding: fma(a, b, 1.5 * 2^23) rounds a b to the nearest integer in one step, and
 // u = fma(a, b, -d0) is a b - d0 rounded once (|u| <= 1/2), so d0 + d1 + d2 follows the exact
 // product rather than fl(a b). Three FP32 operations where a product and digits3 take four.
+// d2 is only ever packed (pack_bf16 keeps the upper 16 bits), so its low half is left uncleared.
 __device__ __forceinline__ void digits3_mul(float a, float b, float& d0, float& d1, float& d2) {
   d0 = __fsub_rn(__fmaf_rn(a, b, 12582912.0f), 12582912.0f);
   const float u = __fmaf_rn(a, b, -d0);
   d1 = hi8_int(u);
   const float u2 = __fsub_rn(u, d1);
-  d2 = hi8_int(u2);
+  d2 = __uint_as_float(__float_as_uint(u2) + 0x8000u);  // rounded; low 16 bits dropped by the pack
 }
 
 // Two BF16-exact FP32 values -> packed bf16x2 (lo in the low half): their upper 16 bits.
@@ -614,11 +615,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           for (int col0 = wg * half; col0 < col_end; col0 += 16) {
             const int cnt = min(16, col_end - col0);  // 16 or 8
             uint32_t r0[16], r1[16];
-            tmem_ld_x8(tl + col0, *reinterpret_cast<uint32_t(*)[8]>(&r0[0]));
-            tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
             if (cnt == 16) {
-              tmem_ld_x8(tl + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r0[8]));
-              tmem_ld_x8(tl + TMEM_L12 + col0 + 8, *reinterpret_cast<uint32_t(*)[8]>(&r1[8]));
+              tmem_ld_x16(tl + col0, r0);
+              tmem_ld_x16(tl + TMEM_L12 + col0, r1);
+            } else {
+              tmem_ld_x8(tl + col0, *reinterpret_cast<uint32_t(*)[8]>(&r0[0]));
+              tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
             }
             tmem_ld_wait();
             if (piece) {
