@@ -43,8 +43,9 @@ constexpr int KB_PER_CH = CHR / KBR;      // 64
 constexpr int TI = 64;                    // rows I per tile (M = 128)
 constexpr int A_PLANE = 128 * KBK * 2;    // bytes of one digit plane of one A K-block (8 KB)
 constexpr int A_STAGE = 3 * A_PLANE;      // 24 KB
-constexpr int NS = 4;                     // load pipeline stages
-constexpr int NSB = 2;                    // B operand stages
+constexpr int NS = 4;                     // load pipeline stages (A planes, raw column values, weights)
+constexpr int NSB = 2;                    // built-B stages (3 B stages with 3 load stages measured slower)
+constexpr size_t kSmemMax = 227 * 1024;
 constexpr int NBG = 256;                  // B-operand / epilogue threads (warps 2..9)
 constexpr int NDR = 64;                   // drainer threads (warps 10, 11): deferred accumulator updates
 constexpr int NTHREADS = 64 + NBG + NDR;
@@ -338,9 +339,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint8_t* sB = sA + NS * A_STAGE;
   float2* sRaw = reinterpret_cast<float2*>(sB + NSB * BSTAGE);
   float* sW = reinterpret_cast<float*>(sRaw + NS * KBR * TJ);
-  float* sScale = sW + NS * KBR * L;
-  int* sExpB = reinterpret_cast<int*>(sScale + 256);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sExpB + 256);
+  float* sScB = sW + NS * KBR * L;  // [2][256] 2^-eB per B column, by chunk parity
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sScB + 512);
   uint64_t* full = bars;             // [NS]   producer -> MMA, B-gen (bulk copies landed)
   uint64_t* empty = full + NS;       // [NS]   MMA commit + 8 B-gen warps -> producer
   uint64_t* bfull = empty + NS;      // [NSB]  8 B-gen warps -> MMA
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint64_t* drained = stashed + 1;   // 2 drainer warps -> epilogue: that stash is in the accumulator
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
   int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [2] builder-warp failure flags, by chunk parity
-  int* sdesc = abortB + 2;  // [4] stash descriptor: kind (0 nothing, 1 whole-tile chunk, 2 end), block, it, jt
+  int* sdesc = abortB + 2;  // [6] stash: kind (0 nothing, 1 whole-tile chunk, 2 end), block, it, jt, chunk, parity
   BlockDesc* sBlk = reinterpret_cast<BlockDesc*>(bars + 32);  // block table, copied from the parameters
   WorkItem* ring = reinterpret_cast<WorkItem*>(sBlk + kMaxBlocks);  // items in flight, producer -> others
 
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         if (kbl == 0 && has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
           const float zm = bjok ? bd.zmax[(size_t)c * bd.n_pad + jt * TJ + bj] : 0.f;
           const int e = scale_exp(bd.wmax[c * L + bl] * zm);
-          sExpB[bn] = e;
+          sScB[(lc & 1) * 256 + bn] = exp2i(-e);
           bsc = exp2i(e);
         }
         if (has_row && !dead) {
@@ -605,6 +605,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           tc_fence_after();
           const int I = it * TI + (m_row % TI);
           const int eA = bd.expA[(size_t)c * bd.n_pad + I];
+          const float* scB = sScB + ((lc - 1) & 1) * 256;  // this chunk's B scales (lc already counts it)
           const bool iok = I < bd.n_pb;
           const bool piece = (cur.flags & 2) != 0;
           const int half = N / 2;  // a multiple of 8
@@ -629,22 +630,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
               for (int jj = 0; jj < 16; ++jj) {
                 const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
                 if (jj < cnt && iok && J < bd.n_pb) {
-                  const double sc = (double)exp2i(-(eA + sExpB[n]));
+                  const double sc = (double)exp2i(-eA) * (double)scB[n];
                   const double x = ((double)__uint_as_float(r0[jj]) + (double)__uint_as_float(r1[jj])) * sc;
                   atomicAdd(bd.acc2 + base + (size_t)l * 2 * nn + (size_t)J * bd.n_pad, x);
                 }
               }
               continue;
             }
-            // whole tile: scale both levels (exact) and stash; the drainers add them to the accumulator
+            // whole tile: stash both levels as they are; the drainers scale them and add them up
             if (ddead) continue;
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj)
-              if (jj < cnt) {
-                const int n = col0 + jj;
-                const float sc = exp2i(-(eA + sExpB[n]));
-                fscr[n * 128 + m_row] = make_float2(__uint_as_float(r0[jj]) * sc, __uint_as_float(r1[jj]) * sc);
-              }
+              if (jj < cnt) fscr[(col0 + jj) * 128 + m_row] = make_float2(__uint_as_float(r0[jj]), __uint_as_float(r1[jj]));
           }
           tc_fence_before();
           __threadfence_block();  // the stash is visible before it is announced
@@ -655,6 +652,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             sdesc[1] = b;
             sdesc[2] = it;
             sdesc[3] = jt;
+            sdesc[4] = c;
+            sdesc[5] = (lc - 1) & 1;
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(stashed);
@@ -688,14 +687,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       if (kind == 2) break;
       if (kind == 1) {
         const BlockDesc& bd = sBlk[sdesc[1]];
-        const int it = sdesc[2], jt = sdesc[3];
+        const int it = sdesc[2], jt = sdesc[3], c = sdesc[4];
+        const float* scB = sScB + sdesc[5] * 256;
         const int I = it * TI + mlo;
         if (I < bd.n_pb) {
+          const float scA = exp2i(-bd.expA[(size_t)c * bd.n_pad + I]);  // the Re and Im rows of I share it
           const size_t nn = (size_t)bd.n_pad * bd.n_pad;
           float2* const acc = bd.acc + I;
           const int jmax = bd.n_pb - jt * TJ;  // tile columns j < jmax lie inside the matrix
           for (int n0 = 0; n0 < N; n0 += 8) {
             float2 x[16], v[16];
+            float sc[8];
             size_t off[8];
             uint32_t okm = 0;
 #pragma unroll
@@ -703,6 +705,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
               const int n = n0 + e, l = n / TJ, j = n - l * TJ;
               if (n < N && j < jmax) {
                 okm |= 1u << e;
+                sc[e] = scA * scB[n];
                 off[e] = (size_t)l * 2 * nn + (size_t)(jt * TJ + j) * bd.n_pad;
                 x[2 * e] = fscr[n * 128 + mlo];
                 x[2 * e + 1] = fscr[n * 128 + mlo + 64];
@@ -713,10 +716,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
 #pragma unroll
             for (int e = 0; e < 8; ++e)
               if (okm & (1u << e)) {
-                df_add(v[2 * e], x[2 * e].x);
-                df_add(v[2 * e], x[2 * e].y);
-                df_add(v[2 * e + 1], x[2 * e + 1].x);
-                df_add(v[2 * e + 1], x[2 * e + 1].y);
+                df_add(v[2 * e], x[2 * e].x * sc[e]);
+                df_add(v[2 * e], x[2 * e].y * sc[e]);
+                df_add(v[2 * e + 1], x[2 * e + 1].x * sc[e]);
+                df_add(v[2 * e + 1], x[2 * e + 1].y * sc[e]);
                 acc[off[e]] = v[2 * e];
                 acc[off[e] + nn] = v[2 * e + 1];
               }
@@ -745,6 +748,11 @@ static int tile_width(int L) {
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static bool herk_set_attributes() {
+  return cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) ==
+         cudaSuccess;
+}
 
 // Device list of the tiles on or above the diagonal for one (n_pb, TJ), cached in the scratch.
 static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, const int2** out, int* count) {
@@ -817,9 +825,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     s.planes_cap = total;
   }
   if (!s.attr_set) {
-    if (cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-        cudaSuccess)
-      return QSGW_ERR_CUDA;
+    if (!herk_set_attributes()) return QSGW_ERR_CUDA;
     s.attr_set = true;
   }
   MainArgs a;
@@ -879,8 +885,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   a.counter = s.counter;
   if (cudaMemsetAsync(s.counter, 0, sizeof(int), stream) != cudaSuccess) return QSGW_ERR_CUDA;
   const int grid = a.n_items < G ? a.n_items : G;
-  const size_t smem = main_smem_bytes(N, TJ, L);
-  herk_mixed_kernel<<<grid, NTHREADS, smem, stream>>>(a);
+  herk_mixed_kernel<<<grid, NTHREADS, main_smem_bytes(N, TJ, L), stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
 }
 
@@ -917,9 +922,7 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   if (!g_noalloc_ptr[dev]) {  // set-up, once per device, with that device current
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return QSGW_ERR_CUDA;
-    if (cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-        cudaSuccess)
-      return QSGW_ERR_CUDA;
+    if (!herk_set_attributes()) return QSGW_ERR_CUDA;
     g_noalloc_ptr[dev] = ptr;
   }
   int n_sm = 0;
