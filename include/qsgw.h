@@ -99,6 +99,16 @@ qsgw_status qsgw_chi0_init(qsgw_ctx **ctx, int n_q, const int *n_pb, int n_omega
 qsgw_status qsgw_chi0_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_unocc,
                                  const double *eps_occ, const double *eps_unocc, int n_omega, const double *omega);
 
+/* Same as qsgw_chi0_accumulate with Z in complex64 (interleaved FP32 re, im; same layout, ldz
+ * in elements), for QSGW_MIXED_BF16X3 contexts only (QSGW_ERR_ARG otherwise). The mixed path
+ * rounds every element of Z to FP32 before it forms digits, so the result is bit-identical to
+ * qsgw_chi0_accumulate on the complex128 data that rounds to this Z. It moves half the bytes
+ * (host staging and HBM reads). The paper's mixed precision likewise holds Z in single
+ * precision; eps and W stay FP64. */
+qsgw_status qsgw_chi0_accumulate_c64(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_unocc,
+                                     const double *eps_occ, const double *eps_unocc, int n_omega,
+                                     const double *omega);
+
 /* One block of transition columns (normally one k-point) for one q-point; see
  * qsgw_chi0_accumulate for the meaning and layout of every field. All pointers device. */
 typedef struct {

@@ -129,8 +129,8 @@ qsgw_status check_grid(const qsgw_ctx* c, int n_omega, const double* omega) {
   return QSGW_OK;
 }
 
-// Core of accumulate once every pointer is on the device.
-qsgw_status accumulate_device(qsgw_ctx* c, int q, const double2* Z, long long ldz, int n_occ, int n_unocc,
+// Core of accumulate once every pointer is on the device. z32: Z holds complex64 (mixed only).
+qsgw_status accumulate_device(qsgw_ctx* c, int q, const void* Z, bool z32, long long ldz, int n_occ, int n_unocc,
                               const double* eo, const double* eu) {
   QAcc& a = c->q[q];
   const long long K = (long long)n_occ * n_unocc;
@@ -138,9 +138,11 @@ qsgw_status accumulate_device(qsgw_ctx* c, int q, const double2* Z, long long ld
     qsgw_status st = grow(reinterpret_cast<void**>(&c->d_w), &c->w_cap, sizeof(double) * (size_t)K * c->g.L);
     if (st != QSGW_OK) return st;
     launch_weights_fp64(eo, eu, n_occ, n_unocc, c->g, c->d_w, K, c->d_err, c->stream);
-    launch_herk_fp64(Z, ldz, a.n_pb, a.n_pad, K, c->d_w, K, c->g.L, static_cast<double2*>(a.acc), c->stream);
+    if (z32) return QSGW_ERR_ARG;
+    launch_herk_fp64(static_cast<const double2*>(Z), ldz, a.n_pb, a.n_pad, K, c->d_w, K, c->g.L,
+                     static_cast<double2*>(a.acc), c->stream);
   } else {
-    qsgw_status st = mixed_accumulate(c->mixed, Z, ldz, a.n_pb, a.n_pad, n_occ, n_unocc, eo, eu, c->g,
+    qsgw_status st = mixed_accumulate(c->mixed, Z, z32, ldz, a.n_pb, a.n_pad, n_occ, n_unocc, eo, eu, c->g,
                                       static_cast<float4*>(a.acc), c->d_err, c->stream);
     if (st != QSGW_OK) return st;
   }
@@ -214,9 +216,14 @@ qsgw_status qsgw_chi0_init(qsgw_ctx** out, int n_q, const int* n_pb, int n_omega
   return QSGW_OK;
 }
 
-qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
-                                 const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
+}  // extern "C"
+
+namespace {
+// qsgw_chi0_accumulate and qsgw_chi0_accumulate_c64: z32 selects complex64 Z.
+qsgw_status accumulate_any(qsgw_ctx* c, int q, const void* Z, bool z32, long long ldz, int n_occ, int n_unocc,
+                           const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
   if (!c || q < 0 || q >= c->n_q || !Z || !eps_occ || !eps_unocc) return QSGW_ERR_ARG;
+  if (z32 && c->prec != QSGW_MIXED_BF16X3) return QSGW_ERR_ARG;
   const QAcc& a = c->q[q];
   if (ldz < a.n_pb || n_occ < 1 || n_unocc < 1) return QSGW_ERR_ARG;
   if ((long long)n_occ * n_unocc > (1LL << 31)) return QSGW_ERR_ARG;
@@ -226,8 +233,7 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ld
 
   const bool z_dev = is_device_ptr(Z);
   const bool e_dev = is_device_ptr(eps_occ) && is_device_ptr(eps_unocc);
-  if (z_dev && e_dev)
-    return accumulate_device(c, q, static_cast<const double2*>(Z), ldz, n_occ, n_unocc, eps_occ, eps_unocc);
+  if (z_dev && e_dev) return accumulate_device(c, q, Z, z32, ldz, n_occ, n_unocc, eps_occ, eps_unocc);
 
   // Host operands go through the next of two staging slots. Outside stream capture their copies
   // run on the context's copy stream, after the kernels that last read that slot but not after
@@ -247,7 +253,7 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ld
   }
   const int s = c->hslot;
   c->hslot ^= 1;
-  const size_t zbytes = z_dev ? 0 : sizeof(double2) * (size_t)ldz * (size_t)K;
+  const size_t zbytes = z_dev ? 0 : (z32 ? sizeof(float2) : sizeof(double2)) * (size_t)ldz * (size_t)K;
   const size_t ebytes = e_dev ? 0 : sizeof(double) * (size_t)(n_occ + n_unocc);
   if (c->hstage_cap[s] < zbytes || c->es_cap[s] < ebytes || c->eb_cap[s] < ebytes) {
     // the slot is about to be reallocated: nothing may still fill or read it
@@ -277,19 +283,33 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ld
     eo = c->d_es[s];
     eu = c->d_es[s] + n_occ;
   }
-  const double2* Zd = static_cast<const double2*>(Z);
+  const void* Zd = Z;
   if (!z_dev) {
     QSGW_CK(cudaMemcpyAsync(c->d_hstage[s], Z, zbytes, cudaMemcpyDefault, cs));
-    Zd = static_cast<const double2*>(c->d_hstage[s]);
+    Zd = c->d_hstage[s];
   }
   if (!capturing) {
     QSGW_CK(cudaEventRecord(c->hcopied[s], cs));
     QSGW_CK(cudaStreamWaitEvent(c->stream, c->hcopied[s], 0));
   }
-  st = accumulate_device(c, q, Zd, ldz, n_occ, n_unocc, eo, eu);
+  st = accumulate_device(c, q, Zd, z32, ldz, n_occ, n_unocc, eo, eu);
   if (st != QSGW_OK) return st;
   if (!capturing) QSGW_CK(cudaEventRecord(c->hfree[s], c->stream));
   return QSGW_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
+                                 const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
+  return accumulate_any(c, q, Z, false, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
+}
+
+qsgw_status qsgw_chi0_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
+                                     const double* eps_occ, const double* eps_unocc, int n_omega,
+                                     const double* omega) {
+  return accumulate_any(c, q, Z, true, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
 }
 
 qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
@@ -304,13 +324,13 @@ qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_blo
     for (int j = 0; j < i; ++j)
       if (blocks[j].q == b.q) return QSGW_ERR_ARG;
     if (!is_device_ptr(b.Z) || !is_device_ptr(b.eps_occ) || !is_device_ptr(b.eps_unocc)) return QSGW_ERR_ARG;
-    mb[i] = MixedBlock{static_cast<const double2*>(b.Z), b.ldz, a.n_pb, a.n_pad, b.n_occ, b.n_unocc, b.eps_occ,
+    mb[i] = MixedBlock{b.Z, b.ldz, a.n_pb, a.n_pad, b.n_occ, b.n_unocc, b.eps_occ,
                        b.eps_unocc, static_cast<float4*>(a.acc)};
   }
   if (c->prec == QSGW_FP64) {
     for (int i = 0; i < n_blocks; ++i) {
       const qsgw_block& b = blocks[i];
-      qsgw_status st = accumulate_device(c, b.q, static_cast<const double2*>(b.Z), b.ldz, b.n_occ, b.n_unocc,
+      qsgw_status st = accumulate_device(c, b.q, b.Z, false, b.ldz, b.n_occ, b.n_unocc,
                                          b.eps_occ, b.eps_unocc);
       if (st != QSGW_OK) return st;
     }
@@ -485,7 +505,7 @@ qsgw_status qsgw_chi0_accumulate_synthetic(qsgw_ctx* c, int q, unsigned long lon
     const int nu = n_unocc_per_k[i];
     auto* Zs = static_cast<double2*>(c->d_zstage);
     launch_synth_z(seed, gen_q, k_begin + i, a.n_pb, n_occ, nu, s_div, Zs, a.n_pb, c->stream);
-    st = accumulate_device(c, q, Zs, a.n_pb, n_occ, nu, eps_occ + (size_t)i * n_occ, eps_unocc + eu_off);
+    st = accumulate_device(c, q, Zs, false, a.n_pb, n_occ, nu, eps_occ + (size_t)i * n_occ, eps_unocc + eu_off);
     if (st != QSGW_OK) return st;
     eu_off += nu;
   }

@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const double* __r
 // the A-operand digit planes written as the exact shared-memory image of each K-block
 // ([plane][k-group 4][row-group 16][8 rows][8 K'] BF16, canonical no-swizzle K-major), and the
 // FP32 copy of Z laid out per J-tile and K-block ([jt][kb][16 r][TJ] float2) for the B side.
-__global__ void __launch_bounds__(256) prep_rows_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
+// TZ: double2 (complex128 input) or float2 (complex64): every element is rounded to FP32 on load.
+template <typename TZ>
+__global__ void __launch_bounds__(256) prep_rows_kernel(const TZ* __restrict__ Z, long long ldz, int n_pb,
                                                         long long K, int n_pad, int n_kb, int TJ, int n_jt,
                                                         uint8_t* __restrict__ aplanes, float2* __restrict__ braw,
                                                         float* __restrict__ zmax, int* __restrict__ expA) {
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const double2* __restric
   for (int jc = q; jc < CHR; jc += 4) {
     const long long r = (long long)c * CHR + jc;
     if (rowok && r < K) {
-      const double2 z = Z[I + r * ldz];
+      const TZ z = Z[I + r * ldz];
       m = fmaxf(m, fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
     }
   }
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const double2* __restric
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const long long r = (long long)kb * KBR + q * 4 + rr;
-      double2 z = make_double2(0.0, 0.0);
+      TZ z{};
       if (rowok && r < K) z = Z[I + r * ldz];
       a[rr] = (float)z.x;
       b[rr] = (float)z.y;
@@ -862,10 +864,16 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     T += d.n_tiles;
     prep_cols_kernel<<<P.n_ch, PC_THREADS, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
                                                  const_cast<float*>(d.wmax), d_err);
-    prep_rows_kernel<<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(B.Z, B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
-                                                                 const_cast<uint8_t*>(d.aplanes),
-                                                                 const_cast<float2*>(d.braw), const_cast<float*>(d.zmax),
-                                                                 const_cast<int*>(d.expA));
+    if (B.z32)
+      prep_rows_kernel<float2><<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(
+          static_cast<const float2*>(B.Z), B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
+          const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw), const_cast<float*>(d.zmax),
+          const_cast<int*>(d.expA));
+    else
+      prep_rows_kernel<double2><<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(
+          static_cast<const double2*>(B.Z), B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
+          const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw), const_cast<float*>(d.zmax),
+          const_cast<int*>(d.expA));
   }
   // whole tiles first; the last R tiles (a partial last wave) are split into P chunk ranges
   const int G = s.n_sm;
@@ -889,10 +897,10 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
 }
 
-qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, int n_pb, int n_pad, int n_occ,
+qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long ldz, int n_pb, int n_pad, int n_occ,
                              int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
                              int* d_err, cudaStream_t stream) {
-  MixedBlock b{Z, ldz, n_pb, n_pad, n_occ, n_unocc, eo, eu, acc};
+  MixedBlock b{Z, ldz, n_pb, n_pad, n_occ, n_unocc, eo, eu, acc, z32};
   return mixed_accumulate_batch(s, 1, &b, g, d_err, stream);
 }
 
@@ -994,7 +1002,7 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   d.n_ch = n_ch;
   prep_cols_kernel<<<n_ch, PC_THREADS, 0, stream>>>(eo, eu, n_unocc, K, g, const_cast<float*>(d.wst),
                                             const_cast<float*>(d.wmax), d_err);
-  prep_rows_kernel<<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt,
+  prep_rows_kernel<double2><<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt,
                                                           const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw),
                                                           const_cast<float*>(d.zmax), const_cast<int*>(d.expA));
   a.fscr = reinterpret_cast<float2*>(base + o_fscr);

@@ -26,19 +26,20 @@ struct MixedScratch {
 // buffer (float2 (hi, lo) planes [L][2 (re, im)][n_pad (J)][n_pad (I)]) followed by an FP64 buffer
 // of the same layout for split tiles; chi0 is their sum.
 struct MixedBlock {
-  const double2* Z;
+  const void* Z;  // complex128 (double2), or complex64 (float2) when z32
   long long ldz;
   int n_pb, n_pad, n_occ, n_unocc;
   const double* eo;
   const double* eu;
   float4* acc;
+  bool z32;  // Z holds complex64: the mixed path rounds every element to FP32 first anyway
 };
 
 // Prep of every block, then one persistent tensor-core launch over all (block, tile, chunk)
 // items. Blocks must belong to distinct q-points (distinct accumulators); at most 32 blocks.
 qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* blocks, const OmegaGrid& g, int* d_err,
                                    cudaStream_t stream);
-qsgw_status mixed_accumulate(MixedScratch& s, const double2* Z, long long ldz, int n_pb, int n_pad, int n_occ,
+qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long ldz, int n_pb, int n_pad, int n_occ,
                              int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
                              int* d_err, cudaStream_t stream);
 void mixed_free(MixedScratch& s);

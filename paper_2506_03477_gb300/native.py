@@ -29,7 +29,7 @@ QSGW_MIXED_TF32X3 = 2  # reserved: rejected with QSGW_ERR_ARG
 EXPORTS = [
     "qsgw_chi0_init", "qsgw_chi0_accumulate", "qsgw_chi0_finalize", "qsgw_eps_inv", "qsgw_chi0_reset",
     "qsgw_chi0_sync", "qsgw_chi0_destroy", "qsgw_status_string", "qsgw_synth_z", "qsgw_chi0_accumulate_synthetic",
-    "qsgw_chi0_accumulate_batch", "qsgw_chi0_block_noalloc",
+    "qsgw_chi0_accumulate_batch", "qsgw_chi0_block_noalloc", "qsgw_chi0_accumulate_c64",
 ]
 
 
@@ -61,6 +61,7 @@ def load():
     sig = {
         "qsgw_chi0_init": [P(_p), _i, P(_i), _i, P(_d), _d, _i, _p],
         "qsgw_chi0_accumulate": [_p, _i, _p, _ll, _i, _i, _p, _p, _i, P(_d)],
+        "qsgw_chi0_accumulate_c64": [_p, _i, _p, _ll, _i, _i, _p, _p, _i, P(_d)],
         "qsgw_chi0_finalize": [_p, _i, _p],
         "qsgw_eps_inv": [_p, _i, _p, _p, _p, _i, P(_i)],
         "qsgw_chi0_reset": [_p, _i],
@@ -125,6 +126,14 @@ def qsgw_chi0_accumulate(ctx: int, q: int, Z, ldz: int, n_occ: int, n_unocc: int
     arr_o = (_d * om.size)(*om.tolist())
     _check(load().qsgw_chi0_accumulate(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eps_occ),
                                        _addr(eps_unocc), om.size, arr_o), "qsgw_chi0_accumulate")
+
+
+def qsgw_chi0_accumulate_c64(ctx: int, q: int, Z, ldz: int, n_occ: int, n_unocc: int, eps_occ, eps_unocc, omega):
+    """Z in complex64 (mixed-precision contexts only; see include/qsgw.h)."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    arr_o = (_d * om.size)(*om.tolist())
+    _check(load().qsgw_chi0_accumulate_c64(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eps_occ),
+                                           _addr(eps_unocc), om.size, arr_o), "qsgw_chi0_accumulate_c64")
 
 
 def qsgw_chi0_finalize(ctx: int, q: int, chi0):

@@ -173,3 +173,50 @@ def test_pinned_host_blocks_double_buffered(N):
     Z = np.concatenate([zt.T for zt, *_ in blocks], axis=1)
     d = np.concatenate([oracle.delta(eo, eu)[0] for _, eo, eu, _, _ in blocks])
     _check_chi(a, oracle.chi0_full(Z, d, wl.omega, wl.spin))
+
+
+def test_complex64_input_is_bit_identical(N):
+    """qsgw_chi0_accumulate_c64: the mixed path rounds Z to FP32 before forming digits, so
+    complex64 input (device or pinned host) gives exactly the complex128 result; FP64 contexts
+    reject it."""
+    n, L = 150, 12
+    wl = Workload("c64", n_q=1, n_k=2, n_occ=5, n_omega=L, s_div=40.0, n_pb_fixed=n, seed=9)
+    shapes = [(5, 700), (3, 250)]
+    blocks = []
+    for k, (no, nu) in enumerate(shapes):
+        zt = z_block(wl.seed, 0, k, n, no, nu, wl.s_div)
+        blocks.append((zt, eps_occ(wl.seed, 0, k, no), eps_unocc(wl.seed, 0, k, nu), no, nu))
+
+    def run(mode):
+        ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+        keep = []
+        try:
+            for zt, eo, eu, no, nu in blocks:
+                EO, EU = _dev(eo), _dev(eu)
+                if mode == "c128":
+                    N.qsgw_chi0_accumulate(ctx, 0, _dev(zt), n, no, nu, EO, EU, wl.omega)
+                else:
+                    z64 = torch.from_numpy(np.ascontiguousarray(zt.astype(np.complex64)))
+                    z64 = z64.cuda() if mode == "c64_dev" else z64.pin_memory()
+                    keep.append(z64)
+                    N.qsgw_chi0_accumulate_c64(ctx, 0, z64, n, no, nu, EO, EU, wl.omega)
+            chi = torch.empty((L, n, n), dtype=torch.complex128, device="cuda")
+            N.qsgw_chi0_finalize(ctx, 0, chi)
+            return chi.cpu().numpy().transpose(0, 2, 1)
+        finally:
+            N.qsgw_chi0_destroy(ctx)
+
+    ref = run("c128")
+    assert np.array_equal(run("c64_dev"), ref)
+    assert np.array_equal(run("c64_host"), ref)
+    Z = np.concatenate([zt.T for zt, *_ in blocks], axis=1)
+    d = np.concatenate([oracle.delta(eo, eu)[0] for _, eo, eu, _, _ in blocks])
+    _check_chi(ref, oracle.chi0_full(Z, d, wl.omega, wl.spin))
+    ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_FP64)
+    try:
+        zt, eo, eu, no, nu = blocks[0]
+        with pytest.raises(N.QsgwError) as e:
+            N.qsgw_chi0_accumulate_c64(ctx, 0, _dev(zt.astype(np.complex64)), n, no, nu, _dev(eo), _dev(eu), wl.omega)
+        assert e.value.status == N.QSGW_ERR_ARG
+    finally:
+        N.qsgw_chi0_destroy(ctx)
