@@ -70,19 +70,13 @@ __device__ __forceinline__ float exp2i(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-// All digit arithmetic stays on the full-rate FP32 pipe (rintf and F2F use the quarter-rate
-// conversion pipe on this part, integer rounding the half-rate ALU pipe). The _rn intrinsics are
-// never contracted into FMAs, which both tricks below rely on.
+// Digit arithmetic. The leading digit is rounded on the FP32 pipe (rintf and F2F would use the
+// quarter-rate conversion pipe); the 8-bit splits use two integer operations each, which measured
+// faster than three FP32 ones. The _rn intrinsics are never contracted into FMAs, which the
+// rounding tricks below rely on.
 // (t + 1.5*2^23) - 1.5*2^23 is t rounded to the nearest integer (ties to even) for |t| < 2^22.
 __device__ __forceinline__ float rint_add(float t) {
   return __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
-}
-// Veltkamp splitting with factor 2^16 + 1: hi = c - (c - x), c = (2^16 + 1) x, keeps the leading
-// 24 - 16 = 8 significant bits of x (round to nearest), so hi is exactly representable in BF16
-// (same exponent range as FP32) and x - hi is exact.
-__device__ __forceinline__ float split_bf16(float x) {
-  const float c = __fmul_rn(65537.0f, x);
-  return __fsub_rn(c, __fsub_rn(c, x));
 }
 
 // Leading 8 significant bits of x, rounded to nearest (ties away from zero), in the integer
