@@ -330,6 +330,51 @@ def run_batched(args):
     print(json.dumps(out))
 
 
+def run_large(args):
+    """The large streamed workload: n_pb = 4000, 64 k-points x 120 x 1200 (K = 9,216,000), 16
+    frequencies (N = 256 per MMA). Z is drawn on the device per k-point inside
+    qsgw_chi0_accumulate_synthetic (one call over all 64 k-points; the Philox draw writes and reads
+    9.2 GB per k-point, ~0.4 % of the call), then eps/W for all 16 frequencies in FP64."""
+    import torch
+    from paper_2506_03477_gb300 import native as N
+    from synthetic import LARGE as G
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    n, Lg, no, nu = G.n_pb(0), G.n_omega, G.n_occ, G.n_unocc_fixed
+    k_cols = G.n_k * no * nu
+    flops = 4.0 * k_cols * n * (n + 1) * Lg
+    ctx = N.qsgw_chi0_init([n], G.omega, G.spin, N.QSGW_MIXED_BF16X3, stream=stream)
+    eo = torch.from_numpy(np.concatenate([eps_occ(G.seed, 0, k, no) for k in range(G.n_k)])).to(dev)
+    eu = torch.from_numpy(np.concatenate([eps_unocc(G.seed, 0, k, nu) for k in range(G.n_k)])).to(dev)
+    v = torch.from_numpy(coulomb_v(G.seed, 0, n)).to(dev)
+    W = torch.empty((Lg, n, n), dtype=torch.complex128, device=dev)
+    N.qsgw_chi0_accumulate_synthetic(ctx, 0, G.seed, 0, 0, 1, no, [nu], eo, eu, G.s_div)  # warm-up, 1 k-point
+    N.qsgw_chi0_sync(ctx)
+    N.qsgw_chi0_reset(ctx, 0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    with ClockSampler(0) as clk:
+        ev[0].record(stream)
+        N.qsgw_chi0_accumulate_synthetic(ctx, 0, G.seed, 0, 0, G.n_k, no, [nu] * G.n_k, eo, eu, G.s_div)
+        ev[1].record(stream)
+        N.qsgw_eps_inv(ctx, 0, v, W, n_omega=Lg)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+    N.qsgw_chi0_destroy(ctx)
+    chi_ms, w_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    sustained = peaks()[0]
+    issued = issued_mma_flops(n, Lg, no * nu) * G.n_k
+    out = {"metric": "large streamed chi0 + W: algorithmic TFLOP/s", "workload": G.name,
+           "value": flops / ((chi_ms + w_ms) * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "chi0_only_tflops": flops / (chi_ms * 1e-3) / 1e12,
+           "tensor_pipe_issued_tflops": issued / (chi_ms * 1e-3) / 1e12,
+           "tensor_pipe_frac": issued / (chi_ms * 1e-3) / 1e12 / sustained,
+           "ms_chi0": chi_ms, "ms_eps_w": w_ms, "flops": flops, "clocks": clk.summary(),
+           "note": "one pass (64 k-points after a 1-k-point warm-up); Z drawn on the device inside the call"}
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ oracle (CPU) legs
 def oracle_inputs(rows):
     """Rows of Z (host generator) and Delta for the sampled chi0 block."""
@@ -403,8 +448,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched"],
-                    help="medium = the benchmark line; batched = the 24-q uneven workload (q-points/s)")
+    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "large"],
+                    help="medium = the benchmark line; batched = the 24-q uneven workload (q-points/s); "
+                         "large = n_pb 4000, 9.2M columns, 16 frequencies (one pass)")
     ap.add_argument("--k-points", type=int, default=64,
                     help="k-points per step (profiling aid for small captures; bench lines use all 64)")
     args = ap.parse_args()
@@ -445,9 +491,9 @@ def main():
                           "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
-    if args.workload == "batched":
+    if args.workload in ("batched", "large"):
         if rank == 0:
-            run_batched(args)
+            (run_batched if args.workload == "batched" else run_large)(args)
         return
     res = run_ours(args, rank, world, local)
     if rank != 0:
@@ -485,15 +531,19 @@ def main():
     print(json.dumps(out))
 
 
-def issued_mma_flops_per_call():
-    """BF16 MMA flops one accumulate call issues (same tiling rules as the library)."""
-    TJ = next(t for t in range(min(256 // L, 32), 0, -1) if (t * L) % 16 == 0)
-    n = TJ * L
-    n_pad = (N_PB + 63) // 64 * 64
-    n_it, n_jt = n_pad // 64, (N_PB + TJ - 1) // TJ
-    tiles = sum(1 for it in range(n_it) for jt in range(n_jt) if jt * TJ + TJ - 1 >= it * 64 and it * 64 < N_PB)
-    n_kb = (N_OCC * N_UNOCC + 15) // 16  # 16-column K-blocks (the last chunk stops at the last column)
+def issued_mma_flops(n_pb, n_omega, k_cols):
+    """BF16 MMA flops one accumulate call over k_cols columns issues (same tiling rules as the library)."""
+    TJ = next(t for t in range(min(256 // n_omega, 32), 0, -1) if (t * n_omega) % 16 == 0)
+    n = TJ * n_omega
+    n_pad = (n_pb + 63) // 64 * 64
+    n_it, n_jt = n_pad // 64, (n_pb + TJ - 1) // TJ
+    tiles = sum(1 for it in range(n_it) for jt in range(n_jt) if jt * TJ + TJ - 1 >= it * 64 and it * 64 < n_pb)
+    n_kb = (k_cols + 15) // 16  # 16-column K-blocks (the last chunk stops at the last column)
     return tiles * n_kb * 2 * 8 * (2.0 * 128 * n * 16)
+
+
+def issued_mma_flops_per_call():
+    return issued_mma_flops(N_PB, L, N_OCC * N_UNOCC)
 
 
 def metric_name():
