@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for chi0(q, i omega), eps and W (ctypes wrapper around oracle.c).
+"""FP64 CPU oracle for chi0(q, i omega), eps and W, and the exchange self-energy (ctypes wrapper
+around oracle.c).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the benchmark's
 CPU-baseline leg. The CUDA library never imports or links it, and the two share no code.
@@ -45,6 +46,8 @@ def _load():
         lib.oracle_eps_w.argtypes = [_c_int, _c_int, _p, _p, _p, _p, _p, _p, _p, _p]
         lib.oracle_cholesky.restype = _c_int
         lib.oracle_cholesky.argtypes = [_c_int, _p, _p]
+        lib.oracle_sigx.restype = None
+        lib.oracle_sigx.argtypes = [_c_int, _p, _c_int, _c_int, _c_ll, _p, _p, _p]
         _lib = lib
     return _lib
 
@@ -85,6 +88,19 @@ def chi0_rows(ZI: np.ndarray, ZJ: np.ndarray, delta_r: np.ndarray, omega: np.nda
 def chi0_full(Zrows: np.ndarray, delta_r: np.ndarray, omega: np.ndarray, spin: float) -> np.ndarray:
     """Full chi0[l, I, J] from Zrows[I, r] = z_{I,r}."""
     return chi0_rows(Zrows, Zrows, delta_r, omega, spin)
+
+
+def sigx(Zrows: np.ndarray, n_occ, n_pb: int, v: np.ndarray) -> np.ndarray:
+    """Exchange self-energy, Eq. (sigx): out[n, m] = -sum_{k,n',mu} conj(Z[n, r]) v[k, mu] Z[m, r]
+    with columns r = (k, n', mu), mu fastest; Zrows has shape (n_qp, n_pb * sum(n_occ))."""
+    Z = np.ascontiguousarray(Zrows, dtype=np.complex128)
+    occ = np.ascontiguousarray(n_occ, dtype=np.int32)
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    n_qp, K = Z.shape
+    assert K == n_pb * int(occ.sum()) and vv.shape == (occ.size, n_pb)
+    out = np.empty((n_qp, n_qp), dtype=np.complex128)  # column-major in C = transposed here
+    _load().oracle_sigx(occ.size, _ptr(occ), int(n_pb), int(n_qp), int(K), _ptr(Z), _ptr(vv), _ptr(out))
+    return np.ascontiguousarray(out.T)
 
 
 def eps_w(chi: np.ndarray, v: np.ndarray, want_eps: bool = True, want_wc: bool = True):

@@ -27,6 +27,9 @@
  *
  * Matrices are column-major per frequency: element (i, j) of frequency l is at
  * l*N*N + j*N + i.
+ *
+ * Also Eq. (sigx) (exchange self-energy), a Hermitian update of the same form with the
+ * Coulomb eigenvalues as column weights: see oracle_sigx.
  */
 #include <complex.h>
 #include <math.h>
@@ -72,6 +75,28 @@ void oracle_chi0_rows(long long K, int nI, const zdouble *ZI, int nJ, const zdou
     }
   }
   free(wl);
+}
+
+/* Eq. (sigx), Sec. 2: the exchange self-energy in the basis of the states at q,
+ *   Sigma^x_{nm}(q) = - sum_k sum_{n' occ} sum_mu conj(Z^{(q-k)n', qn}_{k mu}) v_mu(k) Z^{(q-k)n', qm}_{k mu}.
+ * Z is row-major (n_qp x Ktot): row n holds, for k = 0..n_k-1, n' = 0..n_occ[k]-1 and mu =
+ * 0..n_pb-1 (mu fastest), the value Z^{(q-k)n', qn}_{k mu}; Ktot = n_pb * sum_k n_occ[k].
+ * v is [n_k][n_pb] (the Coulomb eigenvalues v_mu(k) of Eq. (eqvcoue)).
+ * out is column-major n_qp x n_qp: element (n, m) at m * n_qp + n. */
+void oracle_sigx(int n_k, const int *n_occ, int n_pb, int n_qp, long long Ktot, const zdouble *Z, const double *v,
+                 zdouble *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int m = 0; m < n_qp; ++m) {
+    for (int n = 0; n < n_qp; ++n) {
+      zdouble acc = 0.0;
+      long long r = 0;
+      for (int k = 0; k < n_k; ++k)
+        for (int np = 0; np < n_occ[k]; ++np)
+          for (int mu = 0; mu < n_pb; ++mu, ++r)
+            acc += v[(size_t)k * n_pb + mu] * (conj(Z[(size_t)n * Ktot + r]) * Z[(size_t)m * Ktot + r]);
+      out[(size_t)m * n_qp + n] = -acc;
+    }
+  }
 }
 
 /* Eq. (dielectricfunction): eps = I - D chi D with D = diag(sqrt(v)), one frequency. */
