@@ -158,6 +158,34 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx *ctx);
 /* Static, human-readable name of a status code. */
 const char *qsgw_status_string(qsgw_status s);
 
+/* ---- exchange self-energy, Eq. (sigx) (Sec. 2) --------------------------------------------
+ *   Sigma^x_{nm}(q) = - sum_k sum_{n' occ} sum_mu conj(Z^{(q-k)n', qn}_{k mu}) v_mu(k) Z^{(q-k)n', qm}_{k mu}
+ * A Hermitian update of the same form as chi0, with the Coulomb eigenvalues v_mu(k) as column
+ * weights: the rows/columns are the n_qp states n, m at q, the contraction runs over (k, n', mu).
+ * The same tensor-core (or FP64) kernels compute it.
+ *
+ * Create a context for n_q independent q-points with n_qp[q] states each (1 <= n_qp <= 16384);
+ * prec as for qsgw_chi0_init (QSGW_MIXED_BF16X3: <= 1e-6 relative error). qsgw_chi0_finalize
+ * then writes Sigma^x (device complex128 [n_qp][n_qp], column-major, full Hermitian, negative
+ * semidefinite); qsgw_chi0_reset / sync / destroy apply. The chi0-only calls
+ * (qsgw_chi0_accumulate*, qsgw_eps_inv, qsgw_chi0_accumulate_batch / _synthetic) return
+ * QSGW_ERR_STATE on such a context, and qsgw_sigx_accumulate* does on a chi0 context. */
+qsgw_status qsgw_sigx_init(qsgw_ctx **ctx, int n_q, const int *n_qp, qsgw_prec prec, void *cuda_stream);
+
+/* Add one k-point (or any block of occupied states n') to Sigma^x(q).
+ *   Z      device or host, complex128, column-major n_qp[q] x (n_occ * n_pb) with leading
+ *          dimension ldz >= n_qp[q]; column r = n' * n_pb + mu holds Z^{(q-k)n', qn}_{k mu} for
+ *          n = 0 .. n_qp-1 (mu fastest)
+ *   v      device or host [n_pb], v_mu(k) > 0 and finite, else QSGW_ERR_DOMAIN (sticky; those
+ *          columns contribute nothing)
+ * Host arrays follow the same rules as in qsgw_chi0_accumulate. */
+qsgw_status qsgw_sigx_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_pb,
+                                 const double *v);
+/* Same with Z in complex64 (QSGW_MIXED_BF16X3 contexts only; bit-identical to complex128 input
+ * that rounds to this Z, as for qsgw_chi0_accumulate_c64). */
+qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_pb,
+                                     const double *v);
+
 /* ---- allocation-free form (no counterpart in the paper) --------------------------------
  * chi0 of ONE block of transition columns, computed in mixed precision exactly as
  * qsgw_chi0_accumulate + qsgw_chi0_finalize would on a fresh context, but without allocating

@@ -36,6 +36,7 @@ struct qsgw_ctx {
   double omega[kMaxOmega] = {};
   double spin = 2.0;
   qsgw_prec prec = QSGW_FP64;
+  bool sigx = false;  // exchange self-energy context (qsgw_sigx_init): given weights, one weight set
   cudaStream_t stream = nullptr;
   std::vector<QAcc> q;
   int* d_err = nullptr;
@@ -130,19 +131,23 @@ qsgw_status check_grid(const qsgw_ctx* c, int n_omega, const double* omega) {
 }
 
 // Core of accumulate once every pointer is on the device. z32: Z holds complex64 (mixed only).
+// wv: given weights w_r = wv[r mod n_unocc] (exchange self-energy contexts) instead of Delta.
 qsgw_status accumulate_device(qsgw_ctx* c, int q, const void* Z, bool z32, long long ldz, int n_occ, int n_unocc,
-                              const double* eo, const double* eu) {
+                              const double* eo, const double* eu, const double* wv = nullptr) {
   QAcc& a = c->q[q];
   const long long K = (long long)n_occ * n_unocc;
   if (c->prec == QSGW_FP64) {
+    if (z32) return QSGW_ERR_ARG;
     qsgw_status st = grow(reinterpret_cast<void**>(&c->d_w), &c->w_cap, sizeof(double) * (size_t)K * c->g.L);
     if (st != QSGW_OK) return st;
-    launch_weights_fp64(eo, eu, n_occ, n_unocc, c->g, c->d_w, K, c->d_err, c->stream);
-    if (z32) return QSGW_ERR_ARG;
+    if (wv)
+      launch_weights_given_fp64(wv, n_unocc, K, c->d_w, c->d_err, c->stream);
+    else
+      launch_weights_fp64(eo, eu, n_occ, n_unocc, c->g, c->d_w, K, c->d_err, c->stream);
     launch_herk_fp64(static_cast<const double2*>(Z), ldz, a.n_pb, a.n_pad, K, c->d_w, K, c->g.L,
                      static_cast<double2*>(a.acc), c->stream);
   } else {
-    qsgw_status st = mixed_accumulate(c->mixed, Z, z32, ldz, a.n_pb, a.n_pad, n_occ, n_unocc, eo, eu, c->g,
+    qsgw_status st = mixed_accumulate(c->mixed, Z, z32, ldz, a.n_pb, a.n_pad, n_occ, n_unocc, eo, eu, wv, c->g,
                                       static_cast<float4*>(a.acc), c->d_err, c->stream);
     if (st != QSGW_OK) return st;
   }
@@ -219,21 +224,28 @@ qsgw_status qsgw_chi0_init(qsgw_ctx** out, int n_q, const int* n_pb, int n_omega
 }  // extern "C"
 
 namespace {
-// qsgw_chi0_accumulate and qsgw_chi0_accumulate_c64: z32 selects complex64 Z.
+// qsgw_chi0_accumulate(_c64) and qsgw_sigx_accumulate(_c64): z32 selects complex64 Z. For an
+// exchange self-energy context (c->sigx) the columns are (n', mu) with given weights
+// eps_unocc[mu] = v_mu (n_unocc = n_pb of the k-point) and eps_occ is unused.
 qsgw_status accumulate_any(qsgw_ctx* c, int q, const void* Z, bool z32, long long ldz, int n_occ, int n_unocc,
                            const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
-  if (!c || q < 0 || q >= c->n_q || !Z || !eps_occ || !eps_unocc) return QSGW_ERR_ARG;
+  const bool sx = c && c->sigx;
+  if (!c || q < 0 || q >= c->n_q || !Z || (!sx && !eps_occ) || !eps_unocc) return QSGW_ERR_ARG;
   if (z32 && c->prec != QSGW_MIXED_BF16X3) return QSGW_ERR_ARG;
   const QAcc& a = c->q[q];
   if (ldz < a.n_pb || n_occ < 1 || n_unocc < 1) return QSGW_ERR_ARG;
   if ((long long)n_occ * n_unocc > (1LL << 31)) return QSGW_ERR_ARG;
-  qsgw_status st = check_grid(c, n_omega, omega);
+  qsgw_status st = sx ? QSGW_OK : check_grid(c, n_omega, omega);
   if (st != QSGW_OK) return st;
   const long long K = (long long)n_occ * n_unocc;
+  const double* wv = sx ? eps_unocc : nullptr;
+  if (sx) eps_occ = nullptr;
 
   const bool z_dev = is_device_ptr(Z);
-  const bool e_dev = is_device_ptr(eps_occ) && is_device_ptr(eps_unocc);
-  if (z_dev && e_dev) return accumulate_device(c, q, Z, z32, ldz, n_occ, n_unocc, eps_occ, eps_unocc);
+  const bool e_dev = (sx || is_device_ptr(eps_occ)) && is_device_ptr(eps_unocc);
+  if (z_dev && e_dev)
+    return sx ? accumulate_device(c, q, Z, z32, ldz, n_occ, n_unocc, nullptr, nullptr, wv)
+              : accumulate_device(c, q, Z, z32, ldz, n_occ, n_unocc, eps_occ, eps_unocc);
 
   // Host operands go through the next of two staging slots. Outside stream capture their copies
   // run on the context's copy stream, after the kernels that last read that slot but not after
@@ -254,7 +266,8 @@ qsgw_status accumulate_any(qsgw_ctx* c, int q, const void* Z, bool z32, long lon
   const int s = c->hslot;
   c->hslot ^= 1;
   const size_t zbytes = z_dev ? 0 : (z32 ? sizeof(float2) : sizeof(double2)) * (size_t)ldz * (size_t)K;
-  const size_t ebytes = e_dev ? 0 : sizeof(double) * (size_t)(n_occ + n_unocc);
+  const int n_eo = sx ? 0 : n_occ;  // host eps_occ values staged (none for Sigma^x)
+  const size_t ebytes = e_dev ? 0 : sizeof(double) * (size_t)(n_eo + n_unocc);
   if (c->hstage_cap[s] < zbytes || c->es_cap[s] < ebytes || c->eb_cap[s] < ebytes) {
     // the slot is about to be reallocated: nothing may still fill or read it
     QSGW_CK(cudaStreamSynchronize(c->cstream));
@@ -270,18 +283,18 @@ qsgw_status accumulate_any(qsgw_ctx* c, int q, const void* Z, bool z32, long lon
   const double* eo = eps_occ;
   const double* eu = eps_unocc;
   if (!e_dev) {
-    const size_t bo = sizeof(double) * (size_t)n_occ, bu = sizeof(double) * (size_t)n_unocc;
+    const size_t bo = sizeof(double) * (size_t)n_eo, bu = sizeof(double) * (size_t)n_unocc;
     if (!capturing) {
       QSGW_CK(cudaEventSynchronize(c->hcopied[s]));  // the bounce buffer's previous copy is done
-      std::memcpy(c->h_eb[s], eps_occ, bo);
-      std::memcpy(c->h_eb[s] + n_occ, eps_unocc, bu);
+      if (bo) std::memcpy(c->h_eb[s], eps_occ, bo);
+      std::memcpy(c->h_eb[s] + n_eo, eps_unocc, bu);
       QSGW_CK(cudaMemcpyAsync(c->d_es[s], c->h_eb[s], ebytes, cudaMemcpyHostToDevice, cs));
     } else {
-      QSGW_CK(cudaMemcpyAsync(c->d_es[s], eps_occ, bo, cudaMemcpyDefault, cs));
-      QSGW_CK(cudaMemcpyAsync(c->d_es[s] + n_occ, eps_unocc, bu, cudaMemcpyDefault, cs));
+      if (bo) QSGW_CK(cudaMemcpyAsync(c->d_es[s], eps_occ, bo, cudaMemcpyDefault, cs));
+      QSGW_CK(cudaMemcpyAsync(c->d_es[s] + n_eo, eps_unocc, bu, cudaMemcpyDefault, cs));
     }
-    eo = c->d_es[s];
-    eu = c->d_es[s] + n_occ;
+    eo = sx ? nullptr : c->d_es[s];
+    eu = c->d_es[s] + n_eo;
   }
   const void* Zd = Z;
   if (!z_dev) {
@@ -292,7 +305,8 @@ qsgw_status accumulate_any(qsgw_ctx* c, int q, const void* Z, bool z32, long lon
     QSGW_CK(cudaEventRecord(c->hcopied[s], cs));
     QSGW_CK(cudaStreamWaitEvent(c->stream, c->hcopied[s], 0));
   }
-  st = accumulate_device(c, q, Zd, z32, ldz, n_occ, n_unocc, eo, eu);
+  st = sx ? accumulate_device(c, q, Zd, z32, ldz, n_occ, n_unocc, nullptr, nullptr, eu)
+          : accumulate_device(c, q, Zd, z32, ldz, n_occ, n_unocc, eo, eu);
   if (st != QSGW_OK) return st;
   if (!capturing) QSGW_CK(cudaEventRecord(c->hfree[s], c->stream));
   return QSGW_OK;
@@ -303,17 +317,39 @@ extern "C" {
 
 qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
                                  const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
+  if (c && c->sigx) return QSGW_ERR_STATE;
   return accumulate_any(c, q, Z, false, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
 }
 
 qsgw_status qsgw_chi0_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
                                      const double* eps_occ, const double* eps_unocc, int n_omega,
                                      const double* omega) {
+  if (c && c->sigx) return QSGW_ERR_STATE;
   return accumulate_any(c, q, Z, true, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
+}
+
+qsgw_status qsgw_sigx_init(qsgw_ctx** ctx, int n_q, const int* n_qp, qsgw_prec prec, void* cuda_stream) {
+  const double omega0 = 0.0;  // one weight set; the frequency grid is not used
+  qsgw_status st = qsgw_chi0_init(ctx, n_q, n_qp, 1, &omega0, 1.0, prec, cuda_stream);
+  if (st == QSGW_OK) (*ctx)->sigx = true;
+  return st;
+}
+
+qsgw_status qsgw_sigx_accumulate(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_pb,
+                                 const double* v) {
+  if (!c || !c->sigx) return c ? QSGW_ERR_STATE : QSGW_ERR_ARG;
+  return accumulate_any(c, q, Z, false, ldz, n_occ, n_pb, nullptr, v, 0, nullptr);
+}
+
+qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_pb,
+                                     const double* v) {
+  if (!c || !c->sigx) return c ? QSGW_ERR_STATE : QSGW_ERR_ARG;
+  return accumulate_any(c, q, Z, true, ldz, n_occ, n_pb, nullptr, v, 0, nullptr);
 }
 
 qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
   if (!c || n_blocks < 1 || n_blocks > 32 || !blocks) return QSGW_ERR_ARG;
+  if (c->sigx) return QSGW_ERR_STATE;
   MixedBlock mb[32];
   for (int i = 0; i < n_blocks; ++i) {
     const qsgw_block& b = blocks[i];
@@ -353,6 +389,7 @@ qsgw_status qsgw_chi0_finalize(qsgw_ctx* c, int q, void* chi0) {
 qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps_out, int correlation_only,
                          int* info) {
   if (!c || q < 0 || q >= c->n_q || !v || !W || !info) return QSGW_ERR_ARG;
+  if (c->sigx) return QSGW_ERR_STATE;
   const QAcc& a = c->q[q];
   const int n = a.n_pb, L = c->g.L;
   const size_t nn = (size_t)n * n;
@@ -487,6 +524,7 @@ qsgw_status qsgw_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, in
 qsgw_status qsgw_chi0_accumulate_synthetic(qsgw_ctx* c, int q, unsigned long long seed, int gen_q, int k_begin,
                                            int k_end, int n_occ, const int* n_unocc_per_k, const double* eps_occ,
                                            const double* eps_unocc, double s_div) {
+  if (c && c->sigx) return QSGW_ERR_STATE;
   if (!c || q < 0 || q >= c->n_q || k_begin < 0 || k_end <= k_begin || n_occ < 1 || !n_unocc_per_k || !eps_occ ||
       !eps_unocc || !(s_div > 0.0) || gen_q < 0 || gen_q > 0xFFFFFF)
     return QSGW_ERR_ARG;

@@ -27,6 +27,8 @@ inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
 // |w_l(Delta_r)| for one k-point into w[l*ldw + r] (FP64); flags Delta <= 0 / non-finite.
 void launch_weights_fp64(const double* eps_occ, const double* eps_unocc, int n_occ, int n_unocc, const OmegaGrid& g,
                          double* w, long long ldw, int* d_err, cudaStream_t s);
+// w[r] = v[r mod period] (one weight set), domain check v > 0.
+void launch_weights_given_fp64(const double* v, int period, long long K, double* w, int* d_err, cudaStream_t s);
 // acc[l][J][I] += sum_r w[l][r] conj(Z[I,r]) Z[J,r] on upper-triangle 64x64 tiles.
 void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
                       long long ldw, int L, double2* acc, cudaStream_t s);

@@ -33,6 +33,25 @@ void launch_weights_fp64(const double* eps_occ, const double* eps_unocc, int n_o
   weights_fp64_kernel<<<blocks, 256, 0, s>>>(eps_occ, eps_unocc, n_occ, n_unocc, g, w, ldw, d_err);
 }
 
+// Given column weights (one set, L = 1): w[r] = v[r mod period], checked v > 0 and finite. Used
+// for Eq. (sigx), where column r = n' * n_pb + mu carries the Coulomb eigenvalue v_mu(k).
+__global__ void weights_given_fp64_kernel(const double* __restrict__ v, int period, long long K,
+                                          double* __restrict__ w, int* d_err) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < K; r += (long long)gridDim.x * blockDim.x) {
+    const double x = v[r % period];
+    const bool ok = (x > 0.0) && isfinite(x);
+    if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
+    w[r] = ok ? x : 0.0;
+  }
+}
+
+void launch_weights_given_fp64(const double* v, int period, long long K, double* w, int* d_err, cudaStream_t s) {
+  int blocks = (int)((K + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  weights_given_fp64_kernel<<<blocks, 256, 0, s>>>(v, period, K, w, d_err);
+}
+
 constexpr int kT = 64;   // output tile (I and J)
 constexpr int kKS = 16;  // K-step (columns staged per iteration)
 

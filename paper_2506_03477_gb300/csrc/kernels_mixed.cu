@@ -159,6 +159,37 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const double* __r
   }
 }
 
+// Given weights (one set, L = 1): w_r = wv[r mod period] in FP32, checked > 0 and finite, and the
+// per-chunk maximum. One CTA per chunk of CHR columns. (Eq. (sigx): column r = n' * n_pb + mu
+// carries the Coulomb eigenvalue v_mu(k).)
+__global__ void __launch_bounds__(PC_THREADS) prep_cols_given_kernel(const double* __restrict__ wv, int period,
+                                                                     long long K, float* __restrict__ wst,
+                                                                     float* __restrict__ wmax, int* d_err) {
+  __shared__ float red[PC_THREADS / 32];
+  const int c = blockIdx.x, t = threadIdx.x;
+  float wm = 0.f;
+  for (int sub = 0; sub < CHR / PC_THREADS; ++sub) {
+    const long long r = (long long)c * CHR + sub * PC_THREADS + t;
+    float w = 0.f;
+    if (r < K) {
+      const double x = wv[r % period];
+      const bool ok = (x > 0.0) && isfinite(x);
+      if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
+      w = ok ? (float)x : 0.f;
+    }
+    wst[r] = w;
+    wm = fmaxf(wm, w);
+  }
+  for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+  if ((t & 31) == 0) red[t >> 5] = wm;
+  __syncthreads();
+  if (t == 0) {
+    float m = 0.f;
+    for (int w = 0; w < PC_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+    wmax[c] = m;
+  }
+}
+
 // ------------------------------------------------------------------ prep: rows
 // One CTA per (chunk, 64-row tile): chunk maximum of max(|Re z|, |Im z|) per row, its exponent,
 // the A-operand digit planes written as the exact shared-memory image of each K-block
@@ -735,11 +766,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
 }
 
 // ------------------------------------------------------------------ host side
-// J columns per tile: the widest TJ <= 32 with N = TJ * L <= 256 and N % 16 == 0 (MMA shape
-// rule for M = 128). TJ <= 32 bounds the raw-operand stages in shared memory.
+// J columns per tile: the widest TJ with N = TJ * L <= 256, N % 16 == 0 (MMA shape rule for
+// M = 128) and the kernel's shared memory (raw-operand stages grow with TJ) within the limit.
+// L = 12: 20, L = 16: 16, L = 1: 128.
 static int tile_width(int L) {
-  for (int t = (256 / L < 32 ? 256 / L : 32); t >= 1; --t)
-    if ((t * L) % 16 == 0) return t;
+  for (int t = 256 / L; t >= 1; --t)
+    if ((t * L) % 16 == 0 && main_smem_bytes(t * L, t, L) <= kSmemMax) return t;
   return 0;
 }
 
@@ -856,8 +888,12 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     d.n_kbr = (int)((P.K + KBR - 1) / KBR);
     d.n_ch = P.n_ch;
     T += d.n_tiles;
-    prep_cols_kernel<<<P.n_ch, PC_THREADS, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
-                                                 const_cast<float*>(d.wmax), d_err);
+    if (B.wv)
+      prep_cols_given_kernel<<<P.n_ch, PC_THREADS, 0, stream>>>(B.wv, B.n_unocc, P.K, const_cast<float*>(d.wst),
+                                                                const_cast<float*>(d.wmax), d_err);
+    else
+      prep_cols_kernel<<<P.n_ch, PC_THREADS, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
+                                                          const_cast<float*>(d.wmax), d_err);
     if (B.z32)
       prep_rows_kernel<float2><<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(
           static_cast<const float2*>(B.Z), B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
@@ -892,9 +928,9 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
 }
 
 qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long ldz, int n_pb, int n_pad, int n_occ,
-                             int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
-                             int* d_err, cudaStream_t stream) {
-  MixedBlock b{Z, ldz, n_pb, n_pad, n_occ, n_unocc, eo, eu, acc, z32};
+                             int n_unocc, const double* eo, const double* eu, const double* wv, const OmegaGrid& g,
+                             float4* acc, int* d_err, cudaStream_t stream) {
+  MixedBlock b{Z, ldz, n_pb, n_pad, n_occ, n_unocc, eo, eu, acc, z32, wv};
   return mixed_accumulate_batch(s, 1, &b, g, d_err, stream);
 }
 

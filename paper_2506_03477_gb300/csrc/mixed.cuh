@@ -33,6 +33,8 @@ struct MixedBlock {
   const double* eu;
   float4* acc;
   bool z32;  // Z holds complex64: the mixed path rounds every element to FP32 first anyway
+  // Given weights (L = 1) instead of the weights from Delta: w_r = wv[r mod n_unocc], wv > 0.
+  const double* wv;
 };
 
 // Prep of every block, then one persistent tensor-core launch over all (block, tile, chunk)
@@ -40,8 +42,8 @@ struct MixedBlock {
 qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* blocks, const OmegaGrid& g, int* d_err,
                                    cudaStream_t stream);
 qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long ldz, int n_pb, int n_pad, int n_occ,
-                             int n_unocc, const double* eo, const double* eu, const OmegaGrid& g, float4* acc,
-                             int* d_err, cudaStream_t stream);
+                             int n_unocc, const double* eo, const double* eu, const double* wv, const OmegaGrid& g,
+                             float4* acc, int* d_err, cudaStream_t stream);
 void mixed_free(MixedScratch& s);
 // chi0 of one block of columns into `chi0` using only a fixed file-scope device array (no allocation).
 qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_occ, int n_unocc, const double* eo,

@@ -30,6 +30,7 @@ EXPORTS = [
     "qsgw_chi0_init", "qsgw_chi0_accumulate", "qsgw_chi0_finalize", "qsgw_eps_inv", "qsgw_chi0_reset",
     "qsgw_chi0_sync", "qsgw_chi0_destroy", "qsgw_status_string", "qsgw_synth_z", "qsgw_chi0_accumulate_synthetic",
     "qsgw_chi0_accumulate_batch", "qsgw_chi0_block_noalloc", "qsgw_chi0_accumulate_c64",
+    "qsgw_sigx_init", "qsgw_sigx_accumulate", "qsgw_sigx_accumulate_c64",
 ]
 
 
@@ -62,6 +63,9 @@ def load():
         "qsgw_chi0_init": [P(_p), _i, P(_i), _i, P(_d), _d, _i, _p],
         "qsgw_chi0_accumulate": [_p, _i, _p, _ll, _i, _i, _p, _p, _i, P(_d)],
         "qsgw_chi0_accumulate_c64": [_p, _i, _p, _ll, _i, _i, _p, _p, _i, P(_d)],
+        "qsgw_sigx_init": [P(_p), _i, P(_i), _i, _p],
+        "qsgw_sigx_accumulate": [_p, _i, _p, _ll, _i, _i, _p],
+        "qsgw_sigx_accumulate_c64": [_p, _i, _p, _ll, _i, _i, _p],
         "qsgw_chi0_finalize": [_p, _i, _p],
         "qsgw_eps_inv": [_p, _i, _p, _p, _p, _i, P(_i)],
         "qsgw_chi0_reset": [_p, _i],
@@ -134,6 +138,25 @@ def qsgw_chi0_accumulate_c64(ctx: int, q: int, Z, ldz: int, n_occ: int, n_unocc:
     arr_o = (_d * om.size)(*om.tolist())
     _check(load().qsgw_chi0_accumulate_c64(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eps_occ),
                                            _addr(eps_unocc), om.size, arr_o), "qsgw_chi0_accumulate_c64")
+
+
+def qsgw_sigx_init(n_qp, prec: int = QSGW_FP64, stream=None) -> int:
+    """Context for the exchange self-energy, Eq. (sigx) (see include/qsgw.h)."""
+    n_qp = list(n_qp)
+    ctx = _p()
+    arr = (_i * len(n_qp))(*n_qp)
+    _check(load().qsgw_sigx_init(ctypes.byref(ctx), len(n_qp), arr, int(prec), _stream(stream)), "qsgw_sigx_init")
+    return ctx.value
+
+
+def qsgw_sigx_accumulate(ctx: int, q: int, Z, ldz: int, n_occ: int, n_pb: int, v):
+    _check(load().qsgw_sigx_accumulate(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_pb), _addr(v)),
+           "qsgw_sigx_accumulate")
+
+
+def qsgw_sigx_accumulate_c64(ctx: int, q: int, Z, ldz: int, n_occ: int, n_pb: int, v):
+    _check(load().qsgw_sigx_accumulate_c64(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_pb), _addr(v)),
+           "qsgw_sigx_accumulate_c64")
 
 
 def qsgw_chi0_finalize(ctx: int, q: int, chi0):
