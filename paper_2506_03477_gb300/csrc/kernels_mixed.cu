@@ -520,9 +520,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     const int wg = (warp - 2) >> 2;           // column half handled in the epilogue
     const int m_row = quarter * 32 + lane;    // accumulator lane = A row
     const int part = m_row / TI;
-    // B-operand row owned by this thread for the whole kernel (threads bt >= N only help flush)
-    const bool has_row = bt < N;
-    const int bn = has_row ? bt : 0, bl = bn / TJ, bj = bn % TJ;
+    // B-operand row owned by this thread for the whole kernel (threads without one only flush).
+    // With N <= 128 (few frequencies) two threads share a row, each building 8 of its 16 K rows
+    // (K-groups 2 kh and 2 kh + 1), so all builder warps work.
+    const bool split = N <= NBG / 2;
+    const bool has_row = bt < (split ? 2 * N : N);
+    const int bn = has_row ? (split ? bt % N : bt) : 0, bl = bn / TJ, bj = bn % TJ;
+    const int kh = split ? bt / N : -1;  // K half built by this thread (-1: all four K-groups)
     const int boff = (bn >> 3) * 128 + (bn & 7) * 16;
     float bsc = 0.f;
     bool bjok = false;
@@ -571,7 +575,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         if (kbl == 0 && has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
           const float zm = bjok ? bd.zmax[(size_t)c * bd.n_pad + jt * TJ + bj] : 0.f;
           const int e = scale_exp(bd.wmax[c * L + bl] * zm);
-          sScB[(lc & 1) * 256 + bn] = exp2i(-e);
+          if (kh <= 0) sScB[(lc & 1) * 256 + bn] = exp2i(-e);
           bsc = exp2i(e);
         }
         if (has_row && !dead) {
@@ -580,6 +584,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           uint8_t* bdst = sB + sb * BSTAGE + boff;
 #pragma unroll
           for (int kg = 0; kg < 4; ++kg) {
+            if (kh >= 0 && (kg >> 1) != kh) continue;
             float d[3][8];
 #pragma unroll
             for (int rr = 0; rr < 4; ++rr) {
