@@ -273,7 +273,7 @@ struct BlockDesc {
   const float* wmax;
   const int2* tiles;
   float2* acc;    // [l][part][J][I] (hi, lo): whole tiles, each owned by one CTA
-  double* acc2;   // [l][part][J][I] FP64: pieces of the last tiles, added with atomics
+  double* acc2;   // [l][part][J][I] FP64: the reduced pieces of split tiles (piece_reduce_kernel)
   int tile_off;   // first global tile index of this block
   int n_pb, n_pad, n_kb, n_tiles, n_ch;
   int n_kbr;      // K-blocks holding columns (ceil(K / KBR)); the rest of the last chunk is padding
@@ -285,8 +285,9 @@ constexpr int kFscrPerCta = 256 * 128;  // flush scratch pairs per CTA: [column 
 // their row operand) are handed out whole through a global counter, so the CTAs run through them in
 // near lockstep and the row-operand planes of a K-block are read from HBM once and served to the
 // other CTAs of that row tile from L2. The last R tiles (R = T mod #CTAs, or all tiles if T is
-// smaller) are cut into P chunk ranges each, so the final wave keeps every SM busy; such pieces
-// are added to the FP64 accumulator with atomics.
+// smaller) are cut into P chunk ranges each, so the final wave keeps every SM busy. Each piece sums
+// into a private double-float partial buffer; piece_reduce_kernel then adds a tile's P partials, in
+// piece order, to the FP64 accumulator (deterministic, no atomics).
 struct MainArgs {
   BlockDesc blk[kMaxBlocks];
   int nb;
@@ -296,12 +297,14 @@ struct MainArgs {
   uint32_t idesc;
   int* d_err;
   float2* fscr;  // per-CTA flush scratch, kFscrPerCta pairs each (see the chunk epilogue)
+  float2* pbuf;  // per-piece partial sums of split tiles, kFscrPerCta pairs each (double-float)
 };
 
 struct WorkItem {
   int gt;      // global tile index, -1 = none
   int c0, c1;  // chunk range
-  int flags;   // bit 0: last item of this CTA; bit 1: piece (FP64 atomics)
+  int flags;   // bit 0: last item of this CTA; bit 1: piece of a split tile
+  int pid;     // piece index (its partial buffer), -1 for a whole tile
 };
 constexpr int kRing = 4;
 
@@ -322,6 +325,7 @@ __device__ WorkItem decode_item(const MainArgs& p, const BlockDesc* blk, int i) 
   w.gt = -1;
   w.c0 = w.c1 = 0;
   w.flags = 0;
+  w.pid = -1;
   if (i >= p.n_items) return w;
   if (i < p.T_whole) {
     w.gt = i;
@@ -337,6 +341,7 @@ __device__ WorkItem decode_item(const MainArgs& p, const BlockDesc* blk, int i) 
   w.c0 = piece * bd.n_ch / p.P;
   w.c1 = (piece + 1) * bd.n_ch / p.P;
   w.flags = 2;
+  w.pid = j;
   return w;
 }
 
@@ -379,7 +384,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint64_t* drained = stashed + 1;   // 2 drainer warps -> epilogue: that stash is in the accumulator
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
   int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [2] builder-warp failure flags, by chunk parity
-  int* sdesc = abortB + 2;  // [6] stash: kind (0 nothing, 1 whole-tile chunk, 2 end), block, it, jt, chunk, parity
+  int* sdesc = abortB + 2;  // [8] stash: kind (1 whole-tile chunk, 3 piece chunk, 2 end), block, it, jt, chunk,
+                            //     parity, piece, first chunk of the piece
   BlockDesc* sBlk = reinterpret_cast<BlockDesc*>(bars + 32);  // block table, copied from the parameters
   WorkItem* ring = reinterpret_cast<WorkItem*>(sBlk + kMaxBlocks);  // items in flight, producer -> others
 
@@ -635,14 +641,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             }
           }
           tc_fence_after();
-          const int I = it * TI + (m_row % TI);
-          const int eA = bd.expA[(size_t)c * bd.n_pad + I];
-          const float* scB = sScB + ((lc - 1) & 1) * 256;  // this chunk's B scales (lc already counts it)
-          const bool iok = I < bd.n_pb;
           const bool piece = (cur.flags & 2) != 0;
           const int half = N / 2;  // a multiple of 8
-          const size_t nn = (size_t)bd.n_pad * bd.n_pad;
-          const size_t base = (size_t)part * nn + I;
           const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
           const int col_end = (wg + 1) * half;
           for (int col0 = wg * half; col0 < col_end; col0 += 16) {
@@ -656,20 +656,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
               tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
             }
             tmem_ld_wait();
-            if (piece) {
-              // a piece of a split tile: FP64 atomics into the second accumulator
-#pragma unroll
-              for (int jj = 0; jj < 16; ++jj) {
-                const int n = col0 + jj, l = n / TJ, J = jt * TJ + (n - l * TJ);
-                if (jj < cnt && iok && J < bd.n_pb) {
-                  const double sc = (double)exp2i(-eA) * (double)scB[n];
-                  const double x = ((double)__uint_as_float(r0[jj]) + (double)__uint_as_float(r1[jj])) * sc;
-                  atomicAdd(bd.acc2 + base + (size_t)l * 2 * nn + (size_t)J * bd.n_pad, x);
-                }
-              }
-              continue;
-            }
-            // whole tile: stash both levels as they are; the drainers scale them and add them up
+            // stash both levels as they are (whole tile or piece); the drainers scale and add them
             if (ddead) continue;
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj)
@@ -680,12 +667,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           __syncwarp();
           if (lane == 0) mbar_arrive(accempty);
           if (bt == 0) {
-            sdesc[0] = piece ? 0 : 1;
+            sdesc[0] = piece ? 3 : 1;
             sdesc[1] = b;
             sdesc[2] = it;
             sdesc[3] = jt;
             sdesc[4] = c;
             sdesc[5] = (lc - 1) & 1;
+            sdesc[6] = cur.pid;
+            sdesc[7] = c == cur.c0;  // first chunk of the piece: its partial buffer starts here
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(stashed);
@@ -704,10 +693,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     __syncwarp();
     if (lane == 0) mbar_arrive(stashed);
   } else {
-    // ---------------- drainers: double-float read-modify-write of each stashed whole-tile chunk.
+    // ---------------- drainers: double-float read-modify-write of each stashed chunk.
     // Thread (warp dw, lane) owns accumulator lanes m = dw * 32 + lane (Re rows) and m + 64 (Im
     // rows), i.e. row I = it * 64 + m of the tile, for all N columns; 8 columns (16 elements) per
-    // round trip. Each element of a whole tile is written by this CTA only.
+    // round trip. Whole tiles go into the accumulator, each element of which only this CTA
+    // writes; pieces of split tiles go into the piece's own partial buffer ([n][m], as the stash),
+    // written rather than added on the piece's first chunk.
     const int mlo = (warp - 2 - NBG / 32) * 32 + lane;
     const float2* const fscr = p.fscr + (size_t)blockIdx.x * kFscrPerCta;
     for (int nd = 0;; ++nd) {
@@ -717,16 +708,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       }
       const int kind = sdesc[0];
       if (kind == 2) break;
-      if (kind == 1) {
+      if (kind == 1 || kind == 3) {
         const BlockDesc& bd = sBlk[sdesc[1]];
         const int it = sdesc[2], jt = sdesc[3], c = sdesc[4];
         const float* scB = sScB + sdesc[5] * 256;
+        const bool whole = kind == 1, first = !whole && sdesc[7];
         const int I = it * TI + mlo;
-        if (I < bd.n_pb) {
+        const size_t nn = (size_t)bd.n_pad * bd.n_pad;
+        // target of column n, Re row: dst + col_off(n); the Im row is hs further
+        float2* const dst = whole ? bd.acc + I : p.pbuf + (size_t)sdesc[6] * kFscrPerCta + mlo;
+        const size_t hs = whole ? nn : 64;
+        const int jmax = whole ? bd.n_pb - jt * TJ : TJ;  // tile columns j < jmax lie inside the matrix
+        if (!whole || I < bd.n_pb) {
           const float scA = exp2i(-bd.expA[(size_t)c * bd.n_pad + I]);  // the Re and Im rows of I share it
-          const size_t nn = (size_t)bd.n_pad * bd.n_pad;
-          float2* const acc = bd.acc + I;
-          const int jmax = bd.n_pb - jt * TJ;  // tile columns j < jmax lie inside the matrix
           for (int n0 = 0; n0 < N; n0 += 8) {
             float2 x[16], v[16];
             float sc[8];
@@ -738,11 +732,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
               if (n < N && j < jmax) {
                 okm |= 1u << e;
                 sc[e] = scA * scB[n];
-                off[e] = (size_t)l * 2 * nn + (size_t)(jt * TJ + j) * bd.n_pad;
+                off[e] = whole ? (size_t)l * 2 * nn + (size_t)(jt * TJ + j) * bd.n_pad : (size_t)n * 128;
                 x[2 * e] = fscr[n * 128 + mlo];
                 x[2 * e + 1] = fscr[n * 128 + mlo + 64];
-                v[2 * e] = acc[off[e]];
-                v[2 * e + 1] = acc[off[e] + nn];
+                v[2 * e] = first ? make_float2(0.f, 0.f) : dst[off[e]];
+                v[2 * e + 1] = first ? make_float2(0.f, 0.f) : dst[off[e] + hs];
               }
             }
 #pragma unroll
@@ -752,8 +746,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
                 df_add(v[2 * e], x[2 * e].y * sc[e]);
                 df_add(v[2 * e + 1], x[2 * e + 1].x * sc[e]);
                 df_add(v[2 * e + 1], x[2 * e + 1].y * sc[e]);
-                acc[off[e]] = v[2 * e];
-                acc[off[e] + nn] = v[2 * e + 1];
+                dst[off[e]] = v[2 * e];
+                dst[off[e] + hs] = v[2 * e + 1];
               }
           }
         }
@@ -767,6 +761,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
+  }
+}
+
+// After the tensor-core launch: the P piece partials of each split tile r (pieces r * P .. r * P +
+// P - 1), summed in piece order in FP64 and added to the FP64 accumulator, which the readout adds
+// to the double-float one. One CTA row per split tile; no atomics, so the result is deterministic.
+__global__ void __launch_bounds__(256) piece_reduce_kernel(MainArgs p) {
+  const int r = blockIdx.x, gt = p.T_whole + r;
+  const BlockDesc& bd = p.blk[block_of_tile(p.blk, p.nb, gt)];
+  const int2 tile = bd.tiles[gt - bd.tile_off];
+  const int N = p.N, TJ = p.TJ;
+  const size_t nn = (size_t)bd.n_pad * bd.n_pad;
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < N * 128; e += gridDim.y * blockDim.x) {
+    const int n = e >> 7, m = e & 127;
+    const int I = tile.x * TI + (m % TI), part = m / TI, l = n / TJ, J = tile.y * TJ + (n - l * TJ);
+    if (I >= bd.n_pb || J >= bd.n_pb) continue;
+    double sum = 0.0;
+    for (int q = 0; q < p.P; ++q) {
+      const float2 v = p.pbuf[(size_t)(r * p.P + q) * kFscrPerCta + e];
+      sum += (double)v.x + (double)v.y;
+    }
+    bd.acc2[(size_t)part * nn + I + (size_t)l * 2 * nn + (size_t)J * bd.n_pad] += sum;
   }
 }
 
@@ -828,7 +844,8 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
       return QSGW_ERR_CUDA;
   }
   std::vector<Plan> pl(nb);
-  size_t total = align256((size_t)s.n_sm * kFscrPerCta * sizeof(float2));  // flush scratch first
+  const size_t fscr_bytes = align256((size_t)s.n_sm * kFscrPerCta * sizeof(float2));
+  size_t total = 2 * fscr_bytes;  // flush scratch, then the piece partial buffers
   for (int b = 0; b < nb; ++b) {
     Plan& P = pl[b];
     const MixedBlock& B = in[b];
@@ -871,6 +888,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   a.d_err = d_err;
   uint8_t* base = static_cast<uint8_t*>(s.planes);
   a.fscr = reinterpret_cast<float2*>(base);
+  a.pbuf = reinterpret_cast<float2*>(base + fscr_bytes);
   int T = 0, min_ch_tail = 1 << 30;
   for (int b = 0; b < nb; ++b) {
     const Plan& P = pl[b];
@@ -929,6 +947,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   if (cudaMemsetAsync(s.counter, 0, sizeof(int), stream) != cudaSuccess) return QSGW_ERR_CUDA;
   const int grid = a.n_items < G ? a.n_items : G;
   herk_mixed_kernel<<<grid, NTHREADS, main_smem_bytes(N, TJ, L), stream>>>(a);
+  if (R > 0) piece_reduce_kernel<<<dim3(R, (N * 128 + 255) / 256), 256, 0, stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
 }
 
@@ -997,10 +1016,11 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   off += align256((size_t)n_ch * n_pad * sizeof(int));
   const size_t o_wmax = off;
   off += align256((size_t)n_ch * L * sizeof(float));
-  // the rest holds the per-CTA flush scratch; the grid is capped to the CTAs it has room for
+  // the rest holds the per-CTA flush scratch and as many piece partial buffers; the grid is capped
+  // to the CTAs there is room for
   const size_t o_fscr = off, fscr_cta = (size_t)kFscrPerCta * sizeof(float2);
-  if (off + fscr_cta > kNoAllocBytes) return QSGW_ERR_ARG;  // beyond the fixed array: use the context API
-  const int cap_ctas = (int)((kNoAllocBytes - off) / fscr_cta);
+  if (off + 2 * fscr_cta > kNoAllocBytes) return QSGW_ERR_ARG;  // beyond the fixed array: use the context API
+  const int cap_ctas = (int)((kNoAllocBytes - off) / (2 * fscr_cta));
   uint8_t* base = static_cast<uint8_t*>(g_noalloc_ptr[dev]);
   int* d_err = reinterpret_cast<int*>(base);
   int* counter = d_err + 1;
@@ -1041,6 +1061,7 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
                                                           const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw),
                                                           const_cast<float*>(d.zmax), const_cast<int*>(d.expA));
   a.fscr = reinterpret_cast<float2*>(base + o_fscr);
+  a.pbuf = reinterpret_cast<float2*>(base + o_fscr + (size_t)cap_ctas * fscr_cta);
   const int G = n_sm < cap_ctas ? n_sm : cap_ctas, T = n_tiles;
   const int R = T >= G ? T % G : T;
   a.T = T;
@@ -1053,6 +1074,7 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   a.counter = counter;
   const int grid = a.n_items < G ? a.n_items : G;
   herk_mixed_kernel<<<grid, NTHREADS, main_smem_bytes(N, TJ, L), stream>>>(a);
+  if (R > 0) piece_reduce_kernel<<<dim3(R, (N * 128 + 255) / 256), 256, 0, stream>>>(a);
   if (cudaGetLastError() != cudaSuccess) return QSGW_ERR_CUDA;
   launch_finalize_chi(d.acc, ACC_DF32, n_pb, n_pad, L, spin, chi0, stream);
   int h_err = 0;
