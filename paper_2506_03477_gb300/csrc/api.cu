@@ -43,6 +43,8 @@ struct qsgw_ctx {
   // scratch, grown on demand
   double* d_w = nullptr;
   size_t w_cap = 0;  // doubles
+  void* d_part = nullptr;  // FP64 HERK split-K partials
+  size_t part_cap = 0;     // bytes
   void* d_zstage = nullptr;
   size_t zstage_cap = 0;  // bytes
   // host operands: two staging slots filled on a copy stream, so the copies of one block
@@ -144,8 +146,13 @@ qsgw_status accumulate_device(qsgw_ctx* c, int q, const void* Z, bool z32, long 
       launch_weights_given_fp64(wv, n_unocc, K, c->d_w, c->d_err, c->stream);
     else
       launch_weights_fp64(eo, eu, n_occ, n_unocc, c->g, c->d_w, K, c->d_err, c->stream);
-    launch_herk_fp64(static_cast<const double2*>(Z), ldz, a.n_pb, a.n_pad, K, c->d_w, K, c->g.L,
-                     static_cast<double2*>(a.acc), c->stream);
+    const int S = herk_fp64_slices(a.n_pad, c->g.L, K);
+    if (S > 1) {
+      st = grow(&c->d_part, &c->part_cap, sizeof(double2) * (size_t)S * c->g.L * a.n_pad * a.n_pad);
+      if (st != QSGW_OK) return st;
+    }
+    launch_herk_fp64(static_cast<const double2*>(Z), ldz, a.n_pb, a.n_pad, K, c->d_w, K, c->g.L, S,
+                     static_cast<double2*>(a.acc), static_cast<double2*>(c->d_part), c->stream);
   } else {
     qsgw_status st = mixed_accumulate(c->mixed, Z, z32, ldz, a.n_pb, a.n_pad, n_occ, n_unocc, eo, eu, wv, c->g,
                                       static_cast<float4*>(a.acc), c->d_err, c->stream);
@@ -466,6 +473,7 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   for (auto& a : c->q)
     if (a.acc) cudaFree(a.acc);
   if (c->d_w) cudaFree(c->d_w);
+  if (c->d_part) cudaFree(c->d_part);
   if (c->d_zstage) cudaFree(c->d_zstage);
   if (c->cstream) cudaStreamSynchronize(c->cstream);
   for (int i = 0; i < 2; ++i) {

@@ -29,9 +29,12 @@ void launch_weights_fp64(const double* eps_occ, const double* eps_unocc, int n_o
                          double* w, long long ldw, int* d_err, cudaStream_t s);
 // w[r] = v[r mod period] (one weight set), domain check v > 0.
 void launch_weights_given_fp64(const double* v, int period, long long K, double* w, int* d_err, cudaStream_t s);
-// acc[l][J][I] += sum_r w[l][r] conj(Z[I,r]) Z[J,r] on upper-triangle 64x64 tiles.
+// acc[l][J][I] += sum_r w[l][r] conj(Z[I,r]) Z[J,r] on upper-triangle 64x64 tiles. With S > 1 the
+// columns are cut into S slices that sum into part ([S][L][n_pad][n_pad], caller's scratch) and are
+// then added to acc in slice order; herk_fp64_slices picks S (1 unless output tiles are scarce).
+int herk_fp64_slices(int n_pad, int L, long long K);
 void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
-                      long long ldw, int L, double2* acc, cudaStream_t s);
+                      long long ldw, int L, int S, double2* acc, double2* part, cudaStream_t s);
 
 // ---- shared epilogues (kernels_epsw.cu)
 // Accumulator formats: FP64 complex (double2 [l][J][I]) or double-float planes (float2 hi/lo [l][re|im][J][I]).

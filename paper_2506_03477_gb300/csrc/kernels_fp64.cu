@@ -55,12 +55,17 @@ void launch_weights_given_fp64(const double* v, int period, long long K, double*
 constexpr int kT = 64;   // output tile (I and J)
 constexpr int kKS = 16;  // K-step (columns staged per iteration)
 
-// grid: x = J tile, y = I tile, z = frequency. Tiles strictly below the diagonal exit at once.
+// grid: x = J tile, y = I tile, z = frequency + L * K-slice. Tiles strictly below the diagonal exit
+// at once. With S = 1 the tile is added to acc; with S > 1 (few output tiles) slice sk covers
+// columns [K sk / S, K (sk + 1) / S) and stores its tile into its own partial buffer part[sk], which
+// herk_fp64_reduce_kernel then adds to acc in slice order (deterministic).
 __global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
                                                         int n_pad, long long K, const double* __restrict__ w,
-                                                        long long ldw, double2* __restrict__ acc) {
-  const int tj = blockIdx.x, ti = blockIdx.y, l = blockIdx.z;
+                                                        long long ldw, int L, int S, double2* __restrict__ acc,
+                                                        double2* __restrict__ part) {
+  const int tj = blockIdx.x, ti = blockIdx.y, l = blockIdx.z % L, sk = blockIdx.z / L;
   if (tj < ti) return;
+  const long long r_begin = K * sk / S, r_end = K * (sk + 1) / S;
   __shared__ double2 sA[kKS][kT];
   __shared__ double2 sB[kKS][kT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -73,14 +78,14 @@ __global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restric
 #pragma unroll
     for (int b = 0; b < 4; ++b) cr[a][b] = ci[a][b] = 0.0;
 
-  for (long long r0 = 0; r0 < K; r0 += kKS) {
+  for (long long r0 = r_begin; r0 < r_end; r0 += kKS) {
     __syncthreads();
 #pragma unroll
     for (int e = tid; e < kKS * kT; e += 256) {
       const int rr = e / kT, ii = e % kT;
       const long long r = r0 + rr;
       double2 za = make_double2(0.0, 0.0), zb = make_double2(0.0, 0.0);
-      if (r < K) {
+      if (r < r_end) {
         if (i0 + ii < n_pb) za = Z[(i0 + ii) + r * ldz];
         if (j0 + ii < n_pb) {
           const double wr = wl[r];
@@ -113,24 +118,55 @@ __global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restric
         }
     }
   }
-  double2* out = acc + (size_t)l * n_pad * n_pad;
+  const size_t nn = (size_t)n_pad * n_pad;
+  double2* out = S == 1 ? acc + (size_t)l * nn : part + ((size_t)sk * L + l) * nn;
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int I = i0 + ty + 16 * p, J = j0 + tx + 16 * q;
       double2* o = out + (size_t)J * n_pad + I;
-      double2 v = *o;
+      double2 v = S == 1 ? *o : make_double2(0.0, 0.0);
       v.x += cr[p][q];
       v.y += ci[p][q];
       *o = v;
     }
 }
 
+// acc += sum over slices sk = 0 .. S-1 of part[sk], on the upper-triangle tiles; grid as the HERK
+// without the slice dimension.
+__global__ void __launch_bounds__(256) herk_fp64_reduce_kernel(int n_pad, int L, int S, const double2* __restrict__ part,
+                                                               double2* __restrict__ acc) {
+  const int tj = blockIdx.x, ti = blockIdx.y, l = blockIdx.z;
+  if (tj < ti) return;
+  const size_t nn = (size_t)n_pad * n_pad;
+  for (int e = threadIdx.x; e < kT * kT; e += 256) {
+    const size_t o = (size_t)(tj * kT + e / kT) * n_pad + ti * kT + e % kT;
+    double2 v = acc[l * nn + o];
+    for (int sk = 0; sk < S; ++sk) {
+      const double2 x = part[((size_t)sk * L + l) * nn + o];
+      v.x += x.x;
+      v.y += x.y;
+    }
+    acc[l * nn + o] = v;
+  }
+}
+
+int herk_fp64_slices(int n_pad, int L, long long K) {
+  const long long tiles = (long long)(n_pad / kT) * (n_pad / kT + 1) / 2 * L;
+  const long long want = 2 * 152;  // two CTAs per SM of a GB300
+  long long S = tiles >= want ? 1 : (want + tiles - 1) / tiles;
+  const long long steps = (K + kKS - 1) / kKS;
+  if (S > 16) S = 16;
+  if (S > steps) S = steps > 0 ? steps : 1;
+  return (int)S;
+}
+
 void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
-                      long long ldw, int L, double2* acc, cudaStream_t s) {
-  dim3 grid(n_pad / kT, n_pad / kT, L);
-  herk_fp64_kernel<<<grid, 256, 0, s>>>(Z, ldz, n_pb, n_pad, K, w, ldw, acc);
+                      long long ldw, int L, int S, double2* acc, double2* part, cudaStream_t s) {
+  dim3 grid(n_pad / kT, n_pad / kT, L * S);
+  herk_fp64_kernel<<<grid, 256, 0, s>>>(Z, ldz, n_pb, n_pad, K, w, ldw, L, S, acc, part);
+  if (S > 1) herk_fp64_reduce_kernel<<<dim3(n_pad / kT, n_pad / kT, L), 256, 0, s>>>(n_pad, L, S, part, acc);
 }
 
 }  // namespace qsgw
