@@ -1,4 +1,5 @@
-// Mixed-precision chi0 assembly on tcgen05 tensor cores (steps a1-a5).
+// Mixed-precision chi0 assembly on tcgen05 tensor cores (steps a1-a5). The same kernels compute the
+// exchange self-energy of Eq. (sigx), a Hermitian update of the same form with given column weights.
 //
 //   chi0_IJ(l) = -s * sum_r |w_l(Delta_r)| conj(z_{I,r}) z_{J,r},  |w_l| = 2 Delta/(Delta^2 + omega_l^2)
 //   (Sec. 2, Eq. (polfx) at w = i omega; the accumulator holds the positive-weight sum).
@@ -23,10 +24,10 @@
 // sum), which is what bounds CHR: 2048-column chunks measured 1.8e-6 relative on a narrow
 // block, above the 1e-6 bar, against ~0.4e-6 at 1024. The dropped d2 d2 term and the
 // remainders are ~2^-23 of a typical product, at the level of the FP32 rounding of the inputs
-// (d1 d2 alone would be ~2^-20 of a typical product, which is why it is kept). After each chunk both accumulators
-// are scaled by 2^-(eA+eB) (exact) and added into a double-float (2 x FP32) accumulator in
-// global memory; GB300's FP64 rate (~1 TFLOP/s) would make an FP64 read-modify-write here the
-// bottleneck.
+// (d1 d2 alone would be ~2^-20 of a typical product, which is why it is kept). After each chunk
+// both accumulators are stashed, and two drainer warps scale them by 2^-(eA+eB) (exact) and add
+// them into a double-float (2 x FP32) accumulator in global memory while the next chunk's MMAs
+// run; GB300's FP64 rate (~1 TFLOP/s) would make an FP64 read-modify-write here the bottleneck.
 #include <cstring>
 #include <vector>
 
