@@ -186,6 +186,14 @@ qsgw_status qsgw_sigx_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long 
 qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_pb,
                                      const double *v);
 
+/* ---- diagnostics (no counterpart in the paper) ---------------------------------------------
+ * Exercises the bounded device-side wait that every pipeline barrier of the tensor-core kernel
+ * uses: one thread waits on an mbarrier phase that nothing completes and gives up after
+ * limit_seconds (1e-3 .. 2, else QSGW_ERR_ARG). The expected result is QSGW_ERR_TIMEOUT; QSGW_OK
+ * would mean the wait returned without timing out. Synchronises cuda_stream (NULL = legacy
+ * default stream); no GPU fault or hang is involved, and the device stays usable afterwards. */
+qsgw_status qsgw_selftest_wait_timeout(double limit_seconds, void *cuda_stream);
+
 /* ---- allocation-free form (no counterpart in the paper) --------------------------------
  * chi0 of ONE block of transition columns, computed in mixed precision exactly as
  * qsgw_chi0_accumulate + qsgw_chi0_finalize would on a fresh context, but without allocating

@@ -30,7 +30,7 @@ EXPORTS = [
     "qsgw_chi0_init", "qsgw_chi0_accumulate", "qsgw_chi0_finalize", "qsgw_eps_inv", "qsgw_chi0_reset",
     "qsgw_chi0_sync", "qsgw_chi0_destroy", "qsgw_status_string", "qsgw_synth_z", "qsgw_chi0_accumulate_synthetic",
     "qsgw_chi0_accumulate_batch", "qsgw_chi0_block_noalloc", "qsgw_chi0_accumulate_c64",
-    "qsgw_sigx_init", "qsgw_sigx_accumulate", "qsgw_sigx_accumulate_c64",
+    "qsgw_sigx_init", "qsgw_sigx_accumulate", "qsgw_sigx_accumulate_c64", "qsgw_selftest_wait_timeout",
 ]
 
 
@@ -66,6 +66,7 @@ def load():
         "qsgw_sigx_init": [P(_p), _i, P(_i), _i, _p],
         "qsgw_sigx_accumulate": [_p, _i, _p, _ll, _i, _i, _p],
         "qsgw_sigx_accumulate_c64": [_p, _i, _p, _ll, _i, _i, _p],
+        "qsgw_selftest_wait_timeout": [_d, _p],
         "qsgw_chi0_finalize": [_p, _i, _p],
         "qsgw_eps_inv": [_p, _i, _p, _p, _p, _i, P(_i)],
         "qsgw_chi0_reset": [_p, _i],
@@ -157,6 +158,11 @@ def qsgw_sigx_accumulate(ctx: int, q: int, Z, ldz: int, n_occ: int, n_pb: int, v
 def qsgw_sigx_accumulate_c64(ctx: int, q: int, Z, ldz: int, n_occ: int, n_pb: int, v):
     _check(load().qsgw_sigx_accumulate_c64(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_pb), _addr(v)),
            "qsgw_sigx_accumulate_c64")
+
+
+def qsgw_selftest_wait_timeout(limit_seconds: float, stream=None) -> int:
+    """Returns the raw status (QSGW_ERR_TIMEOUT is the expected outcome; see include/qsgw.h)."""
+    return int(load().qsgw_selftest_wait_timeout(float(limit_seconds), _stream(stream)))
 
 
 def qsgw_chi0_finalize(ctx: int, q: int, chi0):
