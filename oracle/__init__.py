@@ -46,6 +46,10 @@ def _load():
         lib.oracle_eps_w.argtypes = [_c_int, _c_int, _p, _p, _p, _p, _p, _p, _p, _p]
         lib.oracle_cholesky.restype = _c_int
         lib.oracle_cholesky.argtypes = [_c_int, _p, _p]
+        lib.oracle_hist_spectral.restype = _c_ll
+        lib.oracle_hist_spectral.argtypes = [_c_ll, _c_int, _p, _c_int, _p, _p, _c_int, _p, _p]
+        lib.oracle_hilbert_weight.restype = _c_double
+        lib.oracle_hilbert_weight.argtypes = [_c_double, _c_double, _c_double]
         lib.oracle_sigx.restype = None
         lib.oracle_sigx.argtypes = [_c_int, _p, _c_int, _c_int, _c_ll, _p, _p, _p]
         _lib = lib
@@ -101,6 +105,38 @@ def sigx(Zrows: np.ndarray, n_occ, n_pb: int, v: np.ndarray) -> np.ndarray:
     out = np.empty((n_qp, n_qp), dtype=np.complex128)  # column-major in C = transposed here
     _load().oracle_sigx(occ.size, _ptr(occ), int(n_pb), int(n_qp), int(K), _ptr(Z), _ptr(vv), _ptr(out))
     return np.ascontiguousarray(out.T)
+
+
+def hist_spectral(ZI: np.ndarray, ZJ: np.ndarray, delta_r: np.ndarray, edges: np.ndarray):
+    """Eq. (impolf) with one bin per column: S[j, i, jj] = sum_{r in bin j} conj(ZI[i, r]) ZJ[jj, r];
+    returns (S, number of columns outside every bin)."""
+    ZI = np.ascontiguousarray(ZI, dtype=np.complex128)
+    ZJ = np.ascontiguousarray(ZJ, dtype=np.complex128)
+    d = np.ascontiguousarray(delta_r, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nI, K = ZI.shape
+    nJ = ZJ.shape[0]
+    out = np.empty((e.size - 1, nJ, nI), dtype=np.complex128)
+    outside = _load().oracle_hist_spectral(K, nI, _ptr(ZI), nJ, _ptr(ZJ), _ptr(d), e.size - 1, _ptr(e), _ptr(out))
+    return np.ascontiguousarray(out.transpose(0, 2, 1)), int(outside)
+
+
+def hilbert_weight(w: float, lo: float, hi: float) -> float:
+    """Eq. (hilbert): (1/(hi-lo)) P.V. int_lo^hi [1/(w - D) - 1/(w + D)] dD, uniform density in the bin."""
+    return _load().oracle_hilbert_weight(float(w), float(lo), float(hi))
+
+
+def real_axis_chi0(S: np.ndarray, edges: np.ndarray, bins_out) -> np.ndarray:
+    """chi0 on the real axis at the centres of the bins in bins_out, from the spectral weights S
+    (Eqs. (impolf), (hilbert)): the Hermitian part sum_j K_j(w) S_j and the anti-Hermitian part
+    -pi S_i / (R_i - L_i) (w in bin i)."""
+    e = np.asarray(edges, dtype=np.float64)
+    out = []
+    for i in bins_out:
+        w = 0.5 * (e[i] + e[i + 1])
+        re = sum(hilbert_weight(w, e[j], e[j + 1]) * S[j] for j in range(S.shape[0]))
+        out.append(re - 1j * np.pi / (e[i + 1] - e[i]) * S[i])
+    return np.array(out)
 
 
 def eps_w(chi: np.ndarray, v: np.ndarray, want_eps: bool = True, want_wc: bool = True):

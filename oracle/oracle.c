@@ -29,7 +29,8 @@
  * l*N*N + j*N + i.
  *
  * Also Eq. (sigx) (exchange self-energy), a Hermitian update of the same form with the
- * Coulomb eigenvalues as column weights: see oracle_sigx.
+ * Coulomb eigenvalues as column weights: see oracle_sigx; and the real-axis route of Eqs.
+ * (impolf) and (hilbert): oracle_hist_spectral, oracle_hilbert_weight.
  */
 #include <complex.h>
 #include <math.h>
@@ -97,6 +98,41 @@ void oracle_sigx(int n_k, const int *n_occ, int n_pb, int n_qp, long long Ktot, 
       out[(size_t)m * n_qp + n] = -acc;
     }
   }
+}
+
+/* Eq. (impolf), Sec. 2, real-axis route: the spectral weight of every histogram bin
+ * [edges[j], edges[j+1]) of transition energies,
+ *   S_j(I, J) = sum over columns r with edges[j] <= Delta_r < edges[j+1] of conj(ZI[i, r]) ZJ[j, r],
+ * so that Im chi0(w) on the real axis is -pi S_j / (edges[j+1] - edges[j]) inside bin j (each
+ * column carries weight 1 into the bin holding its Delta; the paper spreads it with tetrahedron
+ * weights, which need a k-mesh). Columns outside every bin contribute nothing; the count of
+ * such columns is returned. out[(j * nJ + jj) * nI + i], ZI / ZJ row-major as in oracle_chi0_rows. */
+long long oracle_hist_spectral(long long K, int nI, const zdouble *ZI, int nJ, const zdouble *ZJ, const double *delta,
+                               int n_bins, const double *edges, zdouble *out) {
+  int *bin = (int *)malloc((size_t)(K > 0 ? K : 1) * sizeof(int));
+  long long outside = 0;
+  for (long long r = 0; r < K; ++r) {
+    bin[r] = -1;
+    for (int j = 0; j < n_bins; ++j)
+      if (edges[j] <= delta[r] && delta[r] < edges[j + 1]) bin[r] = j;
+    if (bin[r] < 0) ++outside;
+  }
+  for (size_t t = 0; t < (size_t)n_bins * nJ * nI; ++t) out[t] = 0.0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int jj = 0; jj < nJ; ++jj)
+    for (int i = 0; i < nI; ++i)
+      for (long long r = 0; r < K; ++r)
+        if (bin[r] >= 0)
+          out[((size_t)bin[r] * nJ + jj) * nI + i] += conj(ZI[(size_t)i * K + r]) * ZJ[(size_t)jj * K + r];
+  free(bin);
+  return outside;
+}
+
+/* Eq. (hilbert): the Hilbert-transformation weight of bin [L, R) at real frequency w > 0, for a
+ * density uniform inside the bin: (1/(R-L)) P.V. int_L^R [1/(w - D) - 1/(w + D)] dD
+ *   = (1/(R-L)) ln( |w - L| (w + L) / (|w - R| (w + R)) ). */
+double oracle_hilbert_weight(double w, double L, double R) {
+  return log(fabs(w - L) * (w + L) / (fabs(w - R) * (w + R))) / (R - L);
 }
 
 /* Eq. (dielectricfunction): eps = I - D chi D with D = diag(sqrt(v)), one frequency. */
