@@ -186,6 +186,43 @@ qsgw_status qsgw_sigx_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long 
 qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_pb,
                                      const double *v);
 
+/* ---- real-axis route, Eqs. (impolf) and (hilbert) (Sec. 2) ------------------------------------
+ * The paper's own route to chi0: the spectral weight of every histogram bin [edges[j], edges[j+1])
+ * of transition energies,
+ *   S_j(I, J) = sum over columns r = (k, n, m) with Delta_r in bin j of conj(z_{I,r}) z_{J,r},
+ * so that on the real axis Im chi0(w) = -pi s S_j / (edges[j+1] - edges[j]) inside bin j, and the
+ * Hermitian part follows by the Hilbert transformation, Eq. (hilbert). Each column carries weight
+ * 1 into the bin holding its Delta (the paper spreads it with tetrahedron weights, which need a
+ * k-mesh), and the density is taken uniform inside a bin, so the Hilbert weight of bin j at w is
+ * (1/(R-L)) ln(|w-L| (w+L) / (|w-R| (w+R))) with L, R its edges. The spin factor s is left to
+ * the caller.
+ *
+ * Create a context for one q-point: n_pb in [1, 16384]; n_bins in [1, 4096]; edges host
+ * [n_bins + 1], finite, strictly increasing, edges[0] > 0; prec as for qsgw_chi0_init. It holds
+ * one accumulator per bin. qsgw_chi0_reset / sync / destroy apply; the other chi0 calls return
+ * QSGW_ERR_STATE. */
+qsgw_status qsgw_spectral_init(qsgw_ctx **ctx, int n_pb, int n_bins, const double *edges, qsgw_prec prec,
+                               void *cuda_stream);
+
+/* Add one block of transition columns (normally one k-point): Z, ldz, n_occ, n_unocc, eps_occ,
+ * eps_unocc as in qsgw_chi0_accumulate, all on the device. The columns are put in bins by Delta,
+ * gathered bin by bin (a stable counting sort), and every non-empty bin is accumulated by the
+ * chi0 kernels with weight 1. Columns outside every bin contribute nothing; Delta <= 0 or
+ * non-finite sets QSGW_ERR_DOMAIN (sticky). Synchronises once (bin counts). */
+qsgw_status qsgw_spectral_accumulate(qsgw_ctx *ctx, const void *Z, long long ldz, int n_occ, int n_unocc,
+                                     const double *eps_occ, const double *eps_unocc);
+
+/* Write S_j for every bin: device complex128 [n_bins][n_pb][n_pb], column-major, full
+ * Hermitian, positive semidefinite. Synchronises and returns any sticky device error. */
+qsgw_status qsgw_spectral_finalize(qsgw_ctx *ctx, void *S);
+
+/* chi0 on the real axis (without s) at the centres w_o of the bins bins_out[o] (host [n_out],
+ * each in [0, n_bins)), from S as written by qsgw_spectral_finalize (device):
+ *   out[o] = sum_j K_j(w_o) S_j + i (-pi / (R - L)) S_{bins_out[o]},
+ * device complex128 [n_out][n_pb][n_pb]. The Hilbert sum is a library GEMM (cuBLAS DGEMM over the
+ * bins); the anti-Hermitian part is added by a kernel. Synchronises. */
+qsgw_status qsgw_spectral_real_axis(qsgw_ctx *ctx, const void *S, int n_out, const int *bins_out, void *out);
+
 /* ---- diagnostics (no counterpart in the paper) ---------------------------------------------
  * Exercises the bounded device-side wait that every pipeline barrier of the tensor-core kernel
  * uses: one thread waits on an mbarrier phase that nothing completes and gives up after

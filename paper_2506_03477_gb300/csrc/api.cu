@@ -1,5 +1,6 @@
 // C ABI (include/qsgw.h): context, argument validation, host staging, stream ordering, and
 // the eps^{-1} step through cuSOLVER (FP64 Cholesky: potrf + potri, one stream per frequency).
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <cmath>
@@ -37,6 +38,21 @@ struct qsgw_ctx {
   double spin = 2.0;
   qsgw_prec prec = QSGW_FP64;
   bool sigx = false;  // exchange self-energy context (qsgw_sigx_init): given weights, one weight set
+  // real-axis route (qsgw_spectral_init): one accumulator ("q") per histogram bin of Delta
+  bool spectral = false;
+  int n_bins = 0;
+  std::vector<double> edges;  // host [n_bins + 1]
+  double* d_edges = nullptr;
+  double* d_one = nullptr;  // the weight 1 of every column
+  int* d_offsets = nullptr;  // [n_bins + 1] (counts first, then exclusive offsets)
+  int* d_counts = nullptr;
+  void* d_bins = nullptr;
+  size_t bins_cap = 0;
+  void* d_perm = nullptr;
+  size_t perm_cap = 0;
+  void* d_zsort = nullptr;
+  size_t zsort_cap = 0;
+  cublasHandle_t blas = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<QAcc> q;
   int* d_err = nullptr;
@@ -324,14 +340,14 @@ extern "C" {
 
 qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
                                  const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
-  if (c && c->sigx) return QSGW_ERR_STATE;
+  if (c && (c->sigx || c->spectral)) return QSGW_ERR_STATE;
   return accumulate_any(c, q, Z, false, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
 }
 
 qsgw_status qsgw_chi0_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
                                      const double* eps_occ, const double* eps_unocc, int n_omega,
                                      const double* omega) {
-  if (c && c->sigx) return QSGW_ERR_STATE;
+  if (c && (c->sigx || c->spectral)) return QSGW_ERR_STATE;
   return accumulate_any(c, q, Z, true, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
 }
 
@@ -356,7 +372,7 @@ qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long lon
 
 qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
   if (!c || n_blocks < 1 || n_blocks > 32 || !blocks) return QSGW_ERR_ARG;
-  if (c->sigx) return QSGW_ERR_STATE;
+  if (c->sigx || c->spectral) return QSGW_ERR_STATE;
   MixedBlock mb[32];
   for (int i = 0; i < n_blocks; ++i) {
     const qsgw_block& b = blocks[i];
@@ -396,7 +412,7 @@ qsgw_status qsgw_chi0_finalize(qsgw_ctx* c, int q, void* chi0) {
 qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps_out, int correlation_only,
                          int* info) {
   if (!c || q < 0 || q >= c->n_q || !v || !W || !info) return QSGW_ERR_ARG;
-  if (c->sigx) return QSGW_ERR_STATE;
+  if (c->sigx || c->spectral) return QSGW_ERR_STATE;
   const QAcc& a = c->q[q];
   const int n = a.n_pb, L = c->g.L;
   const size_t nn = (size_t)n * n;
@@ -475,6 +491,10 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   if (c->d_w) cudaFree(c->d_w);
   if (c->d_part) cudaFree(c->d_part);
   if (c->d_zstage) cudaFree(c->d_zstage);
+  for (void* p : {(void*)c->d_edges, (void*)c->d_one, (void*)c->d_offsets, (void*)c->d_counts, c->d_bins, c->d_perm,
+                  c->d_zsort})
+    if (p) cudaFree(p);
+  if (c->blas) cublasDestroy(c->blas);
   if (c->cstream) cudaStreamSynchronize(c->cstream);
   for (int i = 0; i < 2; ++i) {
     if (c->d_hstage[i]) cudaFree(c->d_hstage[i]);
@@ -495,6 +515,154 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   if (c->d_info) cudaFree(c->d_info);
   if (c->d_err) cudaFree(c->d_err);
   delete c;
+  return st;
+}
+
+// ---- real-axis route: Eqs. (impolf) and (hilbert) --------------------------------------------
+qsgw_status qsgw_spectral_init(qsgw_ctx** ctx, int n_pb, int n_bins, const double* edges, qsgw_prec prec,
+                               void* cuda_stream) {
+  if (!ctx) return QSGW_ERR_ARG;
+  *ctx = nullptr;
+  if (n_bins < 1 || n_bins > 4096 || !edges || !(edges[0] > 0.0)) return QSGW_ERR_ARG;
+  for (int j = 0; j <= n_bins; ++j)
+    if (!std::isfinite(edges[j]) || (j > 0 && !(edges[j] > edges[j - 1]))) return QSGW_ERR_ARG;
+  const std::vector<int> npb(n_bins, n_pb);
+  const double omega0 = 0.0;
+  // spin -1: the readout's -s * acc then gives S_j = +acc (the weights are +1)
+  qsgw_status st = qsgw_chi0_init(ctx, n_bins, npb.data(), 1, &omega0, -1.0, prec, cuda_stream);
+  if (st != QSGW_OK) return st;
+  qsgw_ctx* c = *ctx;
+  c->spectral = true;
+  c->n_bins = n_bins;
+  c->edges.assign(edges, edges + n_bins + 1);
+  const double one = 1.0;
+  cudaError_t e = cudaMalloc(&c->d_edges, sizeof(double) * (n_bins + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_one, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_offsets, sizeof(int) * (n_bins + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counts, sizeof(int) * n_bins);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_edges, edges, sizeof(double) * (n_bins + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_one, &one, sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    qsgw_chi0_destroy(c);
+    *ctx = nullptr;
+    return cuda_status(e);
+  }
+  return QSGW_OK;
+}
+
+qsgw_status qsgw_spectral_accumulate(qsgw_ctx* c, const void* Z, long long ldz, int n_occ, int n_unocc,
+                                     const double* eps_occ, const double* eps_unocc) {
+  if (!c || !Z || !eps_occ || !eps_unocc || n_occ < 1 || n_unocc < 1) return QSGW_ERR_ARG;
+  if (!c->spectral) return QSGW_ERR_STATE;
+  const int n_pb = c->q[0].n_pb;
+  if (ldz < n_pb || (long long)n_occ * n_unocc > (1LL << 31)) return QSGW_ERR_ARG;
+  if (!is_device_ptr(Z) || !is_device_ptr(eps_occ) || !is_device_ptr(eps_unocc)) return QSGW_ERR_ARG;
+  const long long K = (long long)n_occ * n_unocc;
+  qsgw_status st = grow(&c->d_bins, &c->bins_cap, sizeof(int) * (size_t)K);
+  if (st == QSGW_OK) st = grow(&c->d_perm, &c->perm_cap, sizeof(int) * (size_t)K);
+  if (st != QSGW_OK) return st;
+  launch_hist_sort(eps_occ, eps_unocc, n_occ, n_unocc, c->d_edges, c->n_bins, static_cast<int*>(c->d_bins),
+                   c->d_counts, c->d_offsets, static_cast<int*>(c->d_perm), c->d_err, c->stream);
+  std::vector<int> off(c->n_bins + 1);
+  QSGW_CK(cudaMemcpyAsync(off.data(), c->d_offsets, sizeof(int) * (c->n_bins + 1), cudaMemcpyDeviceToHost,
+                          c->stream));
+  QSGW_CK(cudaStreamSynchronize(c->stream));
+  const int n_in = off[c->n_bins];
+  if (n_in == 0) return QSGW_OK;
+  st = grow(&c->d_zsort, &c->zsort_cap, sizeof(double2) * (size_t)n_pb * n_in);
+  if (st != QSGW_OK) return st;
+  double2* Zs = static_cast<double2*>(c->d_zsort);
+  launch_gather_cols(static_cast<const double2*>(Z), ldz, n_pb, static_cast<const int*>(c->d_perm), n_in, Zs,
+                     c->stream);
+  // every non-empty bin is a block of columns with weight 1 (n_occ = count, n_unocc = 1)
+  MixedBlock mb[32];
+  int nb = 0;
+  for (int j = 0; j < c->n_bins; ++j) {
+    const int cnt = off[j + 1] - off[j];
+    if (cnt == 0) continue;
+    const QAcc& a = c->q[j];
+    const double2* Zj = Zs + (size_t)off[j] * n_pb;
+    if (c->prec == QSGW_FP64) {
+      st = accumulate_device(c, j, Zj, false, n_pb, cnt, 1, nullptr, nullptr, c->d_one);
+      if (st != QSGW_OK) return st;
+      continue;
+    }
+    mb[nb++] = MixedBlock{Zj, n_pb, a.n_pb, a.n_pad, cnt, 1, nullptr, nullptr, static_cast<float4*>(a.acc), false,
+                          c->d_one};
+    if (nb == 32) {
+      st = mixed_accumulate_batch(c->mixed, nb, mb, c->g, c->d_err, c->stream);
+      if (st != QSGW_OK) return st;
+      nb = 0;
+    }
+  }
+  if (nb > 0) st = mixed_accumulate_batch(c->mixed, nb, mb, c->g, c->d_err, c->stream);
+  if (st != QSGW_OK) return st;
+  return cuda_status(cudaGetLastError());
+}
+
+qsgw_status qsgw_spectral_finalize(qsgw_ctx* c, void* S) {
+  if (!c || !S) return QSGW_ERR_ARG;
+  if (!c->spectral) return QSGW_ERR_STATE;
+  const size_t nn = (size_t)c->q[0].n_pb * c->q[0].n_pb;
+  for (int j = 0; j < c->n_bins; ++j) {
+    const QAcc& a = c->q[j];
+    launch_finalize_chi(a.acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, a.n_pb, a.n_pad, 1, c->spin,
+                        static_cast<double2*>(S) + (size_t)j * nn, c->stream);
+  }
+  QSGW_CK(cudaGetLastError());
+  return take_device_error(c);
+}
+
+qsgw_status qsgw_spectral_real_axis(qsgw_ctx* c, const void* S, int n_out, const int* bins_out, void* out) {
+  if (!c || !S || !out || n_out < 1 || !bins_out) return QSGW_ERR_ARG;
+  if (!c->spectral) return QSGW_ERR_STATE;
+  const int nb = c->n_bins;
+  for (int o = 0; o < n_out; ++o)
+    if (bins_out[o] < 0 || bins_out[o] >= nb) return QSGW_ERR_ARG;
+  const int n_pb = c->q[0].n_pb;
+  const long long nn = (long long)n_pb * n_pb;
+  // Hilbert weights of every bin at the output frequencies (bin centres), FP64 on the host:
+  // (1/(R-L)) P.V. int_L^R [1/(w-D) - 1/(w+D)] dD for a density uniform in the bin
+  std::vector<double> Kw((size_t)n_out * nb), coef(n_out);
+  for (int o = 0; o < n_out; ++o) {
+    const int i = bins_out[o];
+    const double w = 0.5 * (c->edges[i] + c->edges[i + 1]);
+    coef[o] = -M_PI / (c->edges[i + 1] - c->edges[i]);
+    for (int j = 0; j < nb; ++j) {
+      const double L = c->edges[j], R = c->edges[j + 1];
+      Kw[(size_t)j * n_out + o] = std::log(std::fabs(w - L) * (w + L) / (std::fabs(w - R) * (w + R))) / (R - L);
+    }
+  }
+  double *dK = nullptr, *dcoef = nullptr;
+  int* dbins = nullptr;
+  cudaError_t e = cudaMalloc(&dK, sizeof(double) * Kw.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dcoef, sizeof(double) * n_out);
+  if (e == cudaSuccess) e = cudaMalloc(&dbins, sizeof(int) * n_out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dK, Kw.data(), sizeof(double) * Kw.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * n_out, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbins, bins_out, sizeof(int) * n_out, cudaMemcpyHostToDevice, c->stream);
+  qsgw_status st = cuda_status(e);
+  if (st == QSGW_OK && !c->blas && cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) st = QSGW_ERR_CUDA;
+  if (st == QSGW_OK && cublasSetStream(c->blas, c->stream) != CUBLAS_STATUS_SUCCESS) st = QSGW_ERR_CUDA;
+  if (st == QSGW_OK) {
+    // Hermitian part, Eq. (hilbert): out (2nn x n_out) = S (2nn x n_bins) * K^T, re and im parts alike
+    const double one = 1.0, zero = 0.0;
+    if (cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)(2 * nn), n_out, nb, &one,
+                    static_cast<const double*>(S), (int)(2 * nn), dK, n_out, &zero, static_cast<double*>(out),
+                    (int)(2 * nn)) != CUBLAS_STATUS_SUCCESS)
+      st = QSGW_ERR_CUDA;
+  }
+  if (st == QSGW_OK) {  // anti-Hermitian part, Eq. (impolf): -pi S_i / (R_i - L_i)
+    launch_add_antiherm(static_cast<const double2*>(S), nn, n_out, dbins, dcoef, static_cast<double2*>(out),
+                        c->stream);
+    st = cuda_status(cudaGetLastError());
+  }
+  if (st == QSGW_OK) st = cuda_status(cudaStreamSynchronize(c->stream));
+  else cudaStreamSynchronize(c->stream);
+  cudaFree(dK);
+  cudaFree(dcoef);
+  cudaFree(dbins);
   return st;
 }
 
@@ -532,7 +700,7 @@ qsgw_status qsgw_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, in
 qsgw_status qsgw_chi0_accumulate_synthetic(qsgw_ctx* c, int q, unsigned long long seed, int gen_q, int k_begin,
                                            int k_end, int n_occ, const int* n_unocc_per_k, const double* eps_occ,
                                            const double* eps_unocc, double s_div) {
-  if (c && c->sigx) return QSGW_ERR_STATE;
+  if (c && (c->sigx || c->spectral)) return QSGW_ERR_STATE;
   if (!c || q < 0 || q >= c->n_q || k_begin < 0 || k_end <= k_begin || n_occ < 1 || !n_unocc_per_k || !eps_occ ||
       !eps_unocc || !(s_div > 0.0) || gen_q < 0 || gen_q > 0xFFFFFF)
     return QSGW_ERR_ARG;

@@ -48,6 +48,17 @@ void launch_form_eps(const void* acc, AccKind kind, int n, int n_pad, int L, dou
 // In place: lower triangle of eps^{-1} -> full W = D eps^{-1} D (minus diag(v) if wc).
 void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, cudaStream_t s);
 
+// ---- real-axis route (spectral.cu)
+// Bin every column by Delta (edges: device [n_bins + 1]), count per bin, exclusive offsets
+// ([n_bins + 1]) and the stable permutation perm (columns in bin order; offsets[n_bins] of them).
+void launch_hist_sort(const double* eo, const double* eu, int n_occ, int n_unocc, const double* edges, int n_bins,
+                      int* bins, int* counts, int* offsets, int* perm, int* d_err, cudaStream_t s);
+void launch_gather_cols(const double2* Z, long long ldz, int n_pb, const int* perm, int n, double2* Zs,
+                        cudaStream_t s);
+// out[o] += i * coef[o] * S[bins_out[o]] (nn complex elements each).
+void launch_add_antiherm(const double2* S, long long nn, int n_out, const int* bins_out, const double* coef,
+                         double2* out, cudaStream_t s);
+
 // ---- synthetic Z (synth.cu)
 void launch_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, int n_occ, int n_unocc, double s_div,
                     double2* Z, long long ldz, cudaStream_t s);

@@ -1,0 +1,135 @@
+// Real-axis route of chi0 (Eqs. (impolf) and (hilbert), Sec. 2): the transition columns are put
+// in the histogram bins [edges[j], edges[j+1]) holding their energy Delta, gathered bin by bin
+// (pair compaction), and each bin's spectral weight S_j = sum_{r in bin j} conj(z_I,r) z_J,r is a
+// Hermitian update run by the chi0 kernels with weight 1. The kernels here do the binning, a
+// stable counting sort of the columns by bin, the gather, and the anti-Hermitian part of the
+// real-axis chi0 after the Hilbert transformation. Every step is deterministic.
+#include "internal.cuh"
+
+namespace qsgw {
+
+// Bin of every column r = n * n_unocc + m (Delta = eu[m] - eo[n]); -1 outside all bins. Delta <= 0
+// or non-finite sets DEV_DOMAIN.
+__global__ void hist_bin_kernel(const double* __restrict__ eo, const double* __restrict__ eu, int n_occ,
+                                int n_unocc, const double* __restrict__ edges, int n_bins, int* __restrict__ bins,
+                                int* d_err) {
+  const long long K = (long long)n_occ * n_unocc;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < K; r += (long long)gridDim.x * blockDim.x) {
+    const double d = eu[r % n_unocc] - eo[r / n_unocc];
+    if (!(d > 0.0) || !isfinite(d)) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
+    int b = -1;
+    if (d >= edges[0] && d < edges[n_bins]) {  // largest j with edges[j] <= d
+      int lo = 0, hi = n_bins - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (edges[mid] <= d) lo = mid; else hi = mid - 1;
+      }
+      b = lo;
+    }
+    bins[r] = b;
+  }
+}
+
+// One CTA (256 threads) per bin: number of columns in the bin.
+__global__ void __launch_bounds__(256) hist_count_kernel(const int* __restrict__ bins, long long K,
+                                                         int* __restrict__ counts) {
+  __shared__ int part[8];
+  const int j = blockIdx.x;
+  int c = 0;
+  for (long long r = threadIdx.x; r < K; r += 256) c += bins[r] == j;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    counts[j] = t;
+  }
+}
+
+// Exclusive scan of the bin counts (offsets[n_bins] = columns inside all bins); one thread.
+__global__ void hist_scan_kernel(const int* __restrict__ counts, int n_bins, int* __restrict__ offsets) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int s = 0;
+  for (int j = 0; j < n_bins; ++j) {
+    offsets[j] = s;
+    s += counts[j];
+  }
+  offsets[n_bins] = s;
+}
+
+// One CTA (1024 threads) per bin: the bin's columns in increasing r, written to
+// perm[offsets[j] ...] (a stable counting sort: ballot and popc within warps, warp totals in smem).
+__global__ void __launch_bounds__(1024) hist_perm_kernel(const int* __restrict__ bins, long long K,
+                                                         const int* __restrict__ offsets, int* __restrict__ perm) {
+  __shared__ int wsum[32];
+  const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int base = offsets[j];
+  for (long long r0 = 0; r0 < K; r0 += 1024) {
+    const long long r = r0 + t;
+    const bool f = r < K && bins[r] == j;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[w] = __popc(m);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int q = 0; q < 32; ++q) {
+      before += q < w ? wsum[q] : 0;
+      total += wsum[q];
+    }
+    if (f) perm[base + before + __popc(m & ((1u << lane) - 1u))] = (int)r;
+    base += total;
+    __syncthreads();
+  }
+}
+
+// Zs[:, p] = Z[:, perm[p]] for p < n (columns of n_pb complex values; one CTA per column).
+__global__ void __launch_bounds__(256) gather_cols_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
+                                                          const int* __restrict__ perm, double2* __restrict__ Zs) {
+  const long long p = blockIdx.x;
+  const double2* src = Z + (long long)perm[p] * ldz;
+  double2* dst = Zs + p * n_pb;
+  for (int i = threadIdx.x; i < n_pb; i += 256) dst[i] = src[i];
+}
+
+// out[o] += i * coef[o] * S[bins_out[o]] (element-wise, complex), for the anti-Hermitian part of
+// the real-axis chi0: -pi S_i / (R_i - L_i) times i.
+__global__ void add_antiherm_kernel(const double2* __restrict__ S, long long nn, int n_out,
+                                    const int* __restrict__ bins_out, const double* __restrict__ coef,
+                                    double2* __restrict__ out) {
+  const int o = blockIdx.y;
+  const double2* s = S + (long long)bins_out[o] * nn;
+  double2* d = out + (long long)o * nn;
+  const double c = coef[o];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    const double2 x = s[e];
+    double2 y = d[e];
+    y.x -= c * x.y;
+    y.y += c * x.x;
+    d[e] = y;
+  }
+}
+
+void launch_hist_sort(const double* eo, const double* eu, int n_occ, int n_unocc, const double* edges, int n_bins,
+                      int* bins, int* counts, int* offsets, int* perm, int* d_err, cudaStream_t s) {
+  const long long K = (long long)n_occ * n_unocc;
+  int blocks = (int)((K + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  hist_bin_kernel<<<blocks, 256, 0, s>>>(eo, eu, n_occ, n_unocc, edges, n_bins, bins, d_err);
+  hist_count_kernel<<<n_bins, 256, 0, s>>>(bins, K, counts);
+  hist_scan_kernel<<<1, 1, 0, s>>>(counts, n_bins, offsets);
+  hist_perm_kernel<<<n_bins, 1024, 0, s>>>(bins, K, offsets, perm);
+}
+
+void launch_gather_cols(const double2* Z, long long ldz, int n_pb, const int* perm, int n, double2* Zs,
+                        cudaStream_t s) {
+  if (n > 0) gather_cols_kernel<<<n, 256, 0, s>>>(Z, ldz, n_pb, perm, Zs);
+}
+
+void launch_add_antiherm(const double2* S, long long nn, int n_out, const int* bins_out, const double* coef,
+                         double2* out, cudaStream_t s) {
+  long long blocks = (nn + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  add_antiherm_kernel<<<dim3((unsigned)blocks, n_out), 256, 0, s>>>(S, nn, n_out, bins_out, coef, out);
+}
+
+}  // namespace qsgw

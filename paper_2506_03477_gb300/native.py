@@ -31,6 +31,7 @@ EXPORTS = [
     "qsgw_chi0_sync", "qsgw_chi0_destroy", "qsgw_status_string", "qsgw_synth_z", "qsgw_chi0_accumulate_synthetic",
     "qsgw_chi0_accumulate_batch", "qsgw_chi0_block_noalloc", "qsgw_chi0_accumulate_c64",
     "qsgw_sigx_init", "qsgw_sigx_accumulate", "qsgw_sigx_accumulate_c64", "qsgw_selftest_wait_timeout",
+    "qsgw_spectral_init", "qsgw_spectral_accumulate", "qsgw_spectral_finalize", "qsgw_spectral_real_axis",
 ]
 
 
@@ -67,6 +68,10 @@ def load():
         "qsgw_sigx_accumulate": [_p, _i, _p, _ll, _i, _i, _p],
         "qsgw_sigx_accumulate_c64": [_p, _i, _p, _ll, _i, _i, _p],
         "qsgw_selftest_wait_timeout": [_d, _p],
+        "qsgw_spectral_init": [P(_p), _i, _i, P(_d), _i, _p],
+        "qsgw_spectral_accumulate": [_p, _p, _ll, _i, _i, _p, _p],
+        "qsgw_spectral_finalize": [_p, _p],
+        "qsgw_spectral_real_axis": [_p, _p, _i, P(_i), _p],
         "qsgw_chi0_finalize": [_p, _i, _p],
         "qsgw_eps_inv": [_p, _i, _p, _p, _p, _i, P(_i)],
         "qsgw_chi0_reset": [_p, _i],
@@ -158,6 +163,31 @@ def qsgw_sigx_accumulate(ctx: int, q: int, Z, ldz: int, n_occ: int, n_pb: int, v
 def qsgw_sigx_accumulate_c64(ctx: int, q: int, Z, ldz: int, n_occ: int, n_pb: int, v):
     _check(load().qsgw_sigx_accumulate_c64(ctx, q, _addr(Z), int(ldz), int(n_occ), int(n_pb), _addr(v)),
            "qsgw_sigx_accumulate_c64")
+
+
+def qsgw_spectral_init(n_pb: int, edges, prec: int = QSGW_FP64, stream=None) -> int:
+    """Context for the real-axis route (histogram of Delta; see include/qsgw.h)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    arr = (_d * e.size)(*e.tolist())
+    ctx = _p()
+    _check(load().qsgw_spectral_init(ctypes.byref(ctx), int(n_pb), e.size - 1, arr, int(prec), _stream(stream)),
+           "qsgw_spectral_init")
+    return ctx.value
+
+
+def qsgw_spectral_accumulate(ctx: int, Z, ldz: int, n_occ: int, n_unocc: int, eps_occ, eps_unocc):
+    _check(load().qsgw_spectral_accumulate(ctx, _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eps_occ),
+                                           _addr(eps_unocc)), "qsgw_spectral_accumulate")
+
+
+def qsgw_spectral_finalize(ctx: int, S):
+    _check(load().qsgw_spectral_finalize(ctx, _addr(S)), "qsgw_spectral_finalize")
+
+
+def qsgw_spectral_real_axis(ctx: int, S, bins_out, out):
+    b = list(bins_out)
+    arr = (_i * len(b))(*b)
+    _check(load().qsgw_spectral_real_axis(ctx, _addr(S), len(b), arr, _addr(out)), "qsgw_spectral_real_axis")
 
 
 def qsgw_selftest_wait_timeout(limit_seconds: float, stream=None) -> int:

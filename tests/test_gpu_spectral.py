@@ -1,0 +1,106 @@
+"""Real-axis route, Eqs. (impolf) and (hilbert), on the GPU against the FP64 oracle:
+
+* the spectral weights S_j of every histogram bin (FP64 <= 1e-12, mixed <= 1e-6 relative per bin,
+  plus the per-element Cauchy-Schwarz bound of a semidefinite matrix), on ragged shapes with
+  columns outside the bins;
+* chi0 on the real axis at sampled bin centres (Hermitian part from the Hilbert transformation,
+  anti-Hermitian part -pi S_i / width);
+* deterministic: two runs give the same bits; Delta <= 0 reported; chi0-only calls rejected."""
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import eps_occ, eps_unocc, z_block
+
+from test_gpu_fp64 import _dev, rel_fro
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+EDGES = 0.06 * 1.05 ** np.arange(0, 80)  # 79 bins over [0.06, 2.8) Ry; Delta reaches 3.8, so some fall outside
+
+
+@pytest.fixture(scope="module")
+def N():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_03477_gb300 import native
+    native.load()
+    return native
+
+
+def _blocks(n, shapes, seed=17):
+    return [(z_block(seed, 0, k, n, no, nu, 60.0), eps_occ(seed, 0, k, no), eps_unocc(seed, 0, k, nu), no, nu)
+            for k, (no, nu) in enumerate(shapes)]
+
+
+def _gpu_S(N, prec, n, blocks, bins_out=None):
+    ctx = N.qsgw_spectral_init(n, EDGES, prec)
+    try:
+        for zt, eo, eu, no, nu in blocks:
+            N.qsgw_spectral_accumulate(ctx, _dev(zt), n, no, nu, _dev(eo), _dev(eu))
+        nb = EDGES.size - 1
+        S = torch.empty((nb, n, n), dtype=torch.complex128, device="cuda")
+        N.qsgw_spectral_finalize(ctx, S)
+        P = None
+        if bins_out is not None:
+            P = torch.empty((len(bins_out), n, n), dtype=torch.complex128, device="cuda")
+            N.qsgw_spectral_real_axis(ctx, S, bins_out, P)
+            P = P.cpu().numpy().transpose(0, 2, 1)
+        return S.cpu().numpy().transpose(0, 2, 1), P
+    finally:
+        N.qsgw_chi0_destroy(ctx)
+
+
+def _oracle_S(blocks):
+    Z = np.concatenate([zt.T for zt, *_ in blocks], axis=1)
+    d = np.concatenate([oracle.delta(eo, eu)[0] for _, eo, eu, _, _ in blocks])
+    return oracle.hist_spectral(Z, Z, d, EDGES)
+
+
+@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_BF16X3", 1e-6)])
+@pytest.mark.parametrize("n,shapes", [(70, [(5, 130), (3, 61)]), (130, [(9, 300)])])
+def test_spectral_weights_and_real_axis(N, prec_name, tol, n, shapes):
+    blocks = _blocks(n, shapes)
+    ref, outside = _oracle_S(blocks)
+    assert outside > 0
+    bins_out = [5, 33, 60, 78]
+    S, P = _gpu_S(N, getattr(N, prec_name), n, blocks, bins_out)
+    for j in range(ref.shape[0]):
+        nrm = np.linalg.norm(ref[j])
+        if nrm == 0.0:
+            assert np.all(S[j] == 0), j
+            continue
+        assert rel_fro(S[j], ref[j]) <= tol, (j, rel_fro(S[j], ref[j]))
+        dg = np.sqrt(np.abs(np.diag(ref[j])))
+        assert np.all(np.abs(S[j] - ref[j]) <= tol * np.outer(dg, dg) + 1e-300), j
+        assert np.array_equal(S[j], S[j].conj().T)
+    Pref = oracle.real_axis_chi0(ref, EDGES, bins_out)
+    for o in range(len(bins_out)):
+        assert rel_fro(P[o], Pref[o]) <= 10 * tol, (o, rel_fro(P[o], Pref[o]))
+
+
+def test_spectral_deterministic_and_errors(N):
+    n = 64
+    blocks = _blocks(n, [(4, 90), (2, 45)])
+    a, _ = _gpu_S(N, N.QSGW_MIXED_BF16X3, n, blocks)
+    b, _ = _gpu_S(N, N.QSGW_MIXED_BF16X3, n, blocks)
+    assert np.array_equal(a, b)
+    ctx = N.qsgw_spectral_init(n, EDGES, N.QSGW_FP64)
+    try:
+        zt, eo, eu, no, nu = blocks[0]
+        with pytest.raises(N.QsgwError) as e:
+            N.qsgw_chi0_accumulate(ctx, 0, _dev(zt), n, no, nu, _dev(eo), _dev(eu), [0.0])
+        assert e.value.status == N.QSGW_ERR_STATE
+        bad = eu.copy()
+        bad[3] = eo.max() - 0.01  # Delta <= 0 for that column
+        N.qsgw_spectral_accumulate(ctx, _dev(zt), n, no, nu, _dev(eo), _dev(bad))
+        S = torch.empty((EDGES.size - 1, n, n), dtype=torch.complex128, device="cuda")
+        with pytest.raises(N.QsgwError) as e:
+            N.qsgw_spectral_finalize(ctx, S)
+        assert e.value.status == N.QSGW_ERR_DOMAIN
+    finally:
+        N.qsgw_chi0_destroy(ctx)
+    with pytest.raises(N.QsgwError) as e:
+        N.qsgw_spectral_init(n, EDGES[::-1], N.QSGW_FP64)  # edges must increase
+    assert e.value.status == N.QSGW_ERR_ARG
