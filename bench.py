@@ -40,8 +40,8 @@ CONFIG_NAME = "medium chi0+W: n_pb=1500, n_k=64, n_occ=40, n_unocc=400 (K=1,024,
 # DRAM traffic of one herk_mixed_kernel launch of this workload (one k-point), from the ncu
 # capture summarised in profiles/herk_mixed_kernel_medium_one_kpoint.md; valid only for the kernel
 # source it was measured on (sha1 prefix), otherwise reported as null.
-TRAFFIC_BYTES_PER_LAUNCH = 9.313e9
-TRAFFIC_KERNEL_SHA1 = "316570bc5232"
+TRAFFIC_BYTES_PER_LAUNCH = 9.338e9
+TRAFFIC_KERNEL_SHA1 = "cf2c30c5f2e5"
 
 
 def measured_traffic():
@@ -447,6 +447,66 @@ def run_sigx(args):
     print(json.dumps(out_d))
 
 
+def run_realaxis(args):
+    """The real-axis route, Eqs. (impolf) and (hilbert), on the medium workload (n_pb = 1500, 64
+    k-points x 40 x 400 columns): histogram spectral weights on the log mesh 0.04 * 1.03^j Ry
+    (156 bins covering every Delta), then chi0 on the real axis at 12 bin centres. Z resident
+    (complex128); one step = reset + 64 accumulate calls + readout of all S_j + real-axis chi0."""
+    import torch
+    from paper_2506_03477_gb300 import native as N
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    nk = min(args.k_points, N_K)
+    ncol = N_OCC * N_UNOCC
+    edges = 0.04 * 1.03 ** np.arange(0, 157)
+    nb = edges.size - 1
+    Z = torch.empty((nk, ncol, N_PB), dtype=torch.complex128, device=dev)
+    eo = torch.from_numpy(np.stack([eps_occ(WL.seed, 0, k, N_OCC) for k in range(N_K)])).to(dev)
+    eu = torch.from_numpy(np.stack([eps_unocc(WL.seed, 0, k, N_UNOCC) for k in range(N_K)])).to(dev)
+    with torch.cuda.stream(stream):
+        for k in range(nk):
+            N.qsgw_synth_z(WL.seed, 0, k, N_PB, N_OCC, N_UNOCC, WL.s_div, Z[k], N_PB, stream=stream)
+    torch.cuda.synchronize(dev)
+    S = torch.empty((nb, N_PB, N_PB), dtype=torch.complex128, device=dev)
+    bins_out = list(range(20, nb, 12))[:12]
+    P = torch.empty((len(bins_out), N_PB, N_PB), dtype=torch.complex128, device=dev)
+    ctx = N.qsgw_spectral_init(N_PB, edges, N.QSGW_MIXED_BF16X3, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(record):
+        for j in range(nb):
+            N.qsgw_chi0_reset(ctx, j)
+        if record:
+            ev[0].record(stream)
+        for k in range(nk):
+            N.qsgw_spectral_accumulate(ctx, Z[k], N_PB, N_OCC, N_UNOCC, eo[k], eu[k])
+        if record:
+            ev[1].record(stream)
+        N.qsgw_spectral_finalize(ctx, S)
+        if record:
+            ev[2].record(stream)
+        N.qsgw_spectral_real_axis(ctx, S, bins_out, P)
+        if record:
+            ev[3].record(stream)
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step(False)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(0) as clk:
+        step(True)
+        torch.cuda.synchronize(dev)
+    N.qsgw_chi0_destroy(ctx)
+    acc_ms, fin_ms, re_ms = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]))
+    flops = 4.0 * nk * ncol * N_PB * (N_PB + 1)  # every column enters exactly one bin
+    out = {"metric": "real-axis chi0 (Eqs. impolf, hilbert): algorithmic TFLOP/s of the spectral accumulation",
+           "workload": f"medium n_pb={N_PB}, {nk} k x {ncol} columns, {nb} log bins, 12 real-axis outputs",
+           "value": flops / (acc_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_accumulate": acc_ms,
+           "ms_readout_S": fin_ms, "ms_real_axis": re_ms, "flops": flops, "clocks": clk.summary(),
+           "note": "per k-point: bin + stable counting sort + gather, then one persistent launch per 32 bins"}
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ oracle (CPU) legs
 def oracle_inputs(rows):
     """Rows of Z (host generator) and Delta for the sampled chi0 block."""
@@ -522,10 +582,11 @@ def main():
     ap.add_argument("--sigx-occ", type=int, default=276, help="occupied states per k-point for --workload sigx "
                     "(profiling aid; the workload uses 276)")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "large", "sigx"],
+    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "large", "sigx", "realaxis"],
                     help="medium = the benchmark line; batched = the 24-q uneven workload (q-points/s); "
                          "large = n_pb 4000, 9.2M columns, 16 frequencies (one pass); "
-                         "sigx = the exchange self-energy at (InAs)6(GaSb)6 sizes")
+                         "sigx = the exchange self-energy at (InAs)6(GaSb)6 sizes; "
+                         "realaxis = the histogram / Hilbert route on the medium shapes")
     ap.add_argument("--k-points", type=int, default=64,
                     help="k-points per step (profiling aid for small captures; bench lines use all 64)")
     args = ap.parse_args()
@@ -566,9 +627,9 @@ def main():
                           "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
-    if args.workload in ("batched", "large", "sigx"):
+    if args.workload in ("batched", "large", "sigx", "realaxis"):
         if rank == 0:
-            {"batched": run_batched, "large": run_large, "sigx": run_sigx}[args.workload](args)
+            {"batched": run_batched, "large": run_large, "sigx": run_sigx, "realaxis": run_realaxis}[args.workload](args)
         return
     res = run_ours(args, rank, world, local)
     if rank != 0:

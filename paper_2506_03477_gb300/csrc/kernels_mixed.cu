@@ -307,7 +307,13 @@ struct WorkItem {
   int flags;   // bit 0: last item of this CTA; bit 1: piece of a split tile
   int pid;     // piece index (its partial buffer), -1 for a whole tile
 };
-constexpr int kRing = 4;
+// Items in flight, producer -> MMA issuer and builders. The producer publishes item i before its
+// wait on `empty` for that item's first K-block; at that point the consumers have released every
+// K-block up to NS before it, and with it read every item whose first K-block lies there. Since an
+// item has at least one K-block, the slot of item i - kRing is free once kRing >= NS + 1 (with
+// one-K-block items, kRing = NS overwrote an item not yet read).
+constexpr int kRing = 2 * NS;
+static_assert(kRing >= NS + 1, "item ring shorter than the load pipeline");
 
 __device__ __forceinline__ int block_of_tile(const BlockDesc* blk, int nb, int gt) {
   int b = 0;

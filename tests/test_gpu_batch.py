@@ -185,3 +185,34 @@ def test_batched_workload_full_size_sampled(N):
             dg = np.sqrt(np.abs(np.diag(ref[l])))
             assert np.all(np.abs(sub[l] - ref[l]) <= 1e-6 * np.outer(dg, dg)), (q, l)
             assert rel_fro(sub[l], ref[l]) <= 1e-6
+
+
+def test_batch_many_short_items(N):
+    """Many work items of one or two K-blocks (K <= 32 columns) per CTA: 16 q-points of
+    n_pb = 600 at 12 frequencies, about 2,500 tiles per launch, 16 per CTA. The producer
+    publishes items ahead of the consumers by up to NS + 1; this holds only while the item ring is
+    longer than that, which tiles of many K-blocks never tested."""
+    shapes = [(600, 1, nu) for nu in (13, 16, 5, 9, 1, 16, 32, 11, 3, 16, 7, 29, 2, 16, 16, 8)]
+    ctx = N.qsgw_chi0_init([s[0] for s in shapes], OMEGA, 2.0, N.QSGW_MIXED_BF16X3)
+    got = []
+    try:
+        for k in range(2):
+            keep = [(_dev(z_block(3, q, k, n, no, nu, 60.0)), _dev(eps_occ(3, q, k, no)), _dev(eps_unocc(3, q, k, nu)))
+                    for q, (n, no, nu) in enumerate(shapes)]
+            N.qsgw_chi0_accumulate_batch(ctx, [(q, keep[q][0], n, no, nu, keep[q][1], keep[q][2])
+                                               for q, (n, no, nu) in enumerate(shapes)])
+            N.qsgw_chi0_sync(ctx)
+        for q, (n, _, _) in enumerate(shapes):
+            chi = torch.empty((12, n, n), dtype=torch.complex128, device="cuda")
+            N.qsgw_chi0_finalize(ctx, q, chi)
+            got.append(chi.cpu().numpy().transpose(0, 2, 1))
+    finally:
+        N.qsgw_chi0_destroy(ctx)
+    for q, (n, no, nu) in enumerate(shapes):
+        Z = np.concatenate([z_block(3, q, k, n, no, nu, 60.0).T for k in range(2)], 1)
+        d = np.concatenate([oracle.delta(eps_occ(3, q, k, no), eps_unocc(3, q, k, nu))[0] for k in range(2)])
+        ref = oracle.chi0_full(Z, d, OMEGA, 2.0)
+        for l in range(12):
+            assert rel_fro(got[q][l], ref[l]) <= 1e-6, (q, l)
+            dg = np.sqrt(np.abs(np.diag(ref[l])))
+            assert np.all(np.abs(got[q][l] - ref[l]) <= 1e-6 * np.outer(dg, dg)), (q, l)

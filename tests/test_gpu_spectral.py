@@ -34,12 +34,12 @@ def _blocks(n, shapes, seed=17):
             for k, (no, nu) in enumerate(shapes)]
 
 
-def _gpu_S(N, prec, n, blocks, bins_out=None):
-    ctx = N.qsgw_spectral_init(n, EDGES, prec)
+def _gpu_S(N, prec, n, blocks, bins_out=None, edges=EDGES):
+    ctx = N.qsgw_spectral_init(n, edges, prec)
     try:
         for zt, eo, eu, no, nu in blocks:
             N.qsgw_spectral_accumulate(ctx, _dev(zt), n, no, nu, _dev(eo), _dev(eu))
-        nb = EDGES.size - 1
+        nb = edges.size - 1
         S = torch.empty((nb, n, n), dtype=torch.complex128, device="cuda")
         N.qsgw_spectral_finalize(ctx, S)
         P = None
@@ -52,10 +52,10 @@ def _gpu_S(N, prec, n, blocks, bins_out=None):
         N.qsgw_chi0_destroy(ctx)
 
 
-def _oracle_S(blocks):
+def _oracle_S(blocks, edges=EDGES):
     Z = np.concatenate([zt.T for zt, *_ in blocks], axis=1)
     d = np.concatenate([oracle.delta(eo, eu)[0] for _, eo, eu, _, _ in blocks])
-    return oracle.hist_spectral(Z, Z, d, EDGES)
+    return oracle.hist_spectral(Z, Z, d, edges)
 
 
 @pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_BF16X3", 1e-6)])
@@ -104,3 +104,19 @@ def test_spectral_deterministic_and_errors(N):
     with pytest.raises(N.QsgwError) as e:
         N.qsgw_spectral_init(n, EDGES[::-1], N.QSGW_FP64)  # edges must increase
     assert e.value.status == N.QSGW_ERR_ARG
+
+
+def test_spectral_many_sparse_bins(N):
+    """n_pb = 600 over 156 log bins (0.04 * 1.03^j Ry), 3,000 columns: most bins hold one K-block
+    (<= 16 columns) or none, so one launch of 32 bins gives every CTA many one-K-block tiles."""
+    edges = 0.04 * 1.03 ** np.arange(0, 157)
+    blocks = _blocks(600, [(20, 90), (12, 100)], seed=23)
+    ref, _ = _oracle_S(blocks, edges)
+    assert sum(np.linalg.norm(r) > 0 for r in ref) > 64
+    S, _ = _gpu_S(N, N.QSGW_MIXED_BF16X3, 600, blocks, edges=edges)
+    for j in range(ref.shape[0]):
+        nrm = np.linalg.norm(ref[j])
+        if nrm == 0.0:
+            assert np.all(S[j] == 0), j
+            continue
+        assert rel_fro(S[j], ref[j]) <= 1e-6, (j, rel_fro(S[j], ref[j]))
