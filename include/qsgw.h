@@ -199,21 +199,29 @@ qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx *ctx, int q, const void *Z, long l
  *
  * Create a context for one q-point: n_pb in [1, 16384]; n_bins in [1, 4096]; edges host
  * [n_bins + 1], finite, strictly increasing, edges[0] > 0; prec as for qsgw_chi0_init. It holds
- * one accumulator per bin. qsgw_chi0_reset / sync / destroy apply; the other chi0 calls return
- * QSGW_ERR_STATE. */
+ * one accumulator per bin and a staging area per bin for the columns of many accumulate calls:
+ * 4096 columns of n_pb values per bin (complex64 in the mixed precision, complex128 in FP64), fewer
+ * (a multiple of 16, at least 16) where that would exceed 16 GiB in all. QSGW_ERR_NOMEM if the
+ * device cannot hold them. qsgw_chi0_reset(ctx, j) clears bin j, its staged columns included;
+ * sync / destroy apply; the other chi0 calls return QSGW_ERR_STATE. */
 qsgw_status qsgw_spectral_init(qsgw_ctx **ctx, int n_pb, int n_bins, const double *edges, qsgw_prec prec,
                                void *cuda_stream);
 
 /* Add one block of transition columns (normally one k-point): Z, ldz, n_occ, n_unocc, eps_occ,
- * eps_unocc as in qsgw_chi0_accumulate, all on the device. The columns are put in bins by Delta,
- * gathered bin by bin (a stable counting sort), and every non-empty bin is accumulated by the
- * chi0 kernels with weight 1. Columns outside every bin contribute nothing; Delta <= 0 or
- * non-finite sets QSGW_ERR_DOMAIN (sticky). Synchronises once (bin counts). */
+ * eps_unocc as in qsgw_chi0_accumulate, all on the device. The columns are put in bins by Delta
+ * and gathered bin by bin (a stable counting sort) into the bins' staging. A bin whose staging
+ * cannot take its new columns is first accumulated over the staged ones by the chi0 kernels with
+ * weight 1 (a bin with more new columns than its staging holds is accumulated over them at once),
+ * so the tensor-core kernel sees whole 1024-column chunks rather than the few columns one call
+ * puts in a bin. Columns outside every bin contribute
+ * nothing; Delta <= 0 or non-finite sets QSGW_ERR_DOMAIN (sticky). Synchronises once (bin
+ * counts). */
 qsgw_status qsgw_spectral_accumulate(qsgw_ctx *ctx, const void *Z, long long ldz, int n_occ, int n_unocc,
                                      const double *eps_occ, const double *eps_unocc);
 
-/* Write S_j for every bin: device complex128 [n_bins][n_pb][n_pb], column-major, full
- * Hermitian, positive semidefinite. Synchronises and returns any sticky device error. */
+/* Accumulate every bin over its staged columns, then write S_j for every bin: device complex128
+ * [n_bins][n_pb][n_pb], column-major, full Hermitian, positive semidefinite. Accumulation may go
+ * on afterwards. Synchronises and returns any sticky device error. */
 qsgw_status qsgw_spectral_finalize(qsgw_ctx *ctx, void *S);
 
 /* chi0 on the real axis (without s) at the centres w_o of the bins bins_out[o] (host [n_out],

@@ -3,6 +3,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -50,8 +51,15 @@ struct qsgw_ctx {
   size_t bins_cap = 0;
   void* d_perm = nullptr;
   size_t perm_cap = 0;
-  void* d_zsort = nullptr;
+  void* d_zsort = nullptr;  // the columns of bins that overflow their staging in one call
   size_t zsort_cap = 0;
+  // per-bin staging: stage_cols columns of n_pb values per bin (complex64 in the mixed precision,
+  // complex128 in FP64), filled over accumulate calls and flushed as one update per bin
+  void* d_stage = nullptr;
+  int stage_cols = 0;
+  std::vector<int> fill;       // columns staged per bin
+  void** d_dptr = nullptr;     // [n_bins] gather destinations of one call
+  std::vector<void*> h_dptr;
   cublasHandle_t blas = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<QAcc> q;
@@ -334,6 +342,58 @@ qsgw_status accumulate_any(qsgw_ctx* c, int q, const void* Z, bool z32, long lon
   if (!capturing) QSGW_CK(cudaEventRecord(c->hfree[s], c->stream));
   return QSGW_OK;
 }
+
+// ---- real-axis route: per-bin staging
+constexpr int kStageCols = 4096;              // staged columns per bin (four exact FP32 chunks)
+constexpr size_t kStageBudget = 16ull << 30;  // bytes of staging at most; fewer columns per bin beyond
+
+size_t spectral_col_bytes(const qsgw_ctx* c) {
+  return (c->prec == QSGW_FP64 ? sizeof(double2) : sizeof(float2)) * (size_t)c->q[0].n_pb;
+}
+
+struct BinCols {
+  int j;          // bin
+  const void* Z;  // its columns, n_pb values each, consecutive
+  int cnt;
+};
+
+// S_j += sum over the given columns of conj(z_I) z_J (weight 1), for every listed bin: up to 32
+// bins per launch of the tensor-core kernel, or one FP64 update per bin.
+qsgw_status spectral_update(qsgw_ctx* c, const std::vector<BinCols>& v) {
+  const int n_pb = c->q[0].n_pb;
+  MixedBlock mb[32];
+  int nb = 0;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const BinCols& x = v[i];
+    const QAcc& a = c->q[x.j];
+    if (c->prec == QSGW_FP64) {
+      qsgw_status st = accumulate_device(c, x.j, x.Z, false, n_pb, x.cnt, 1, nullptr, nullptr, c->d_one);
+      if (st != QSGW_OK) return st;
+      continue;
+    }
+    mb[nb++] = MixedBlock{x.Z, n_pb, a.n_pb, a.n_pad, x.cnt, 1, nullptr, nullptr, static_cast<float4*>(a.acc), true,
+                          c->d_one};
+    if (nb == 32 || i + 1 == v.size()) {
+      qsgw_status st = mixed_accumulate_batch(c->mixed, nb, mb, c->g, c->d_err, c->stream);
+      if (st != QSGW_OK) return st;
+      nb = 0;
+    }
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// Runs the update of every listed bin over its staged columns and empties its staging.
+qsgw_status spectral_flush(qsgw_ctx* c, const std::vector<int>& js) {
+  const size_t cb = spectral_col_bytes(c);
+  std::vector<BinCols> v;
+  for (int j : js)
+    if (c->fill[j] > 0)
+      v.push_back({j, static_cast<uint8_t*>(c->d_stage) + (size_t)j * c->stage_cols * cb, c->fill[j]});
+  qsgw_status st = spectral_update(c, v);
+  if (st != QSGW_OK) return st;
+  for (int j : js) c->fill[j] = 0;
+  return QSGW_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -473,6 +533,7 @@ qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps
 
 qsgw_status qsgw_chi0_reset(qsgw_ctx* c, int q) {
   if (!c || q < 0 || q >= c->n_q) return QSGW_ERR_ARG;
+  if (c->spectral) c->fill[q] = 0;  // columns staged for the bin belong to the sum being cleared
   QSGW_CK(cudaMemsetAsync(c->q[q].acc, 0, c->q[q].bytes, c->stream));
   return QSGW_OK;
 }
@@ -492,7 +553,7 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   if (c->d_part) cudaFree(c->d_part);
   if (c->d_zstage) cudaFree(c->d_zstage);
   for (void* p : {(void*)c->d_edges, (void*)c->d_one, (void*)c->d_offsets, (void*)c->d_counts, c->d_bins, c->d_perm,
-                  c->d_zsort})
+                  c->d_zsort, c->d_stage, (void*)c->d_dptr})
     if (p) cudaFree(p);
   if (c->blas) cublasDestroy(c->blas);
   if (c->cstream) cudaStreamSynchronize(c->cstream);
@@ -540,13 +601,22 @@ qsgw_status qsgw_spectral_init(qsgw_ctx** ctx, int n_pb, int n_bins, const doubl
   if (e == cudaSuccess) e = cudaMalloc(&c->d_one, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_offsets, sizeof(int) * (n_bins + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_counts, sizeof(int) * n_bins);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_dptr, sizeof(void*) * n_bins);
+  const size_t cb = spectral_col_bytes(c);
+  long long cols = (long long)(kStageBudget / (cb * n_bins));
+  cols = std::min<long long>(kStageCols, cols / 16 * 16);
+  c->stage_cols = (int)std::max<long long>(16, cols);
+  c->fill.assign(n_bins, 0);
+  c->h_dptr.assign(n_bins, nullptr);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_stage, cb * n_bins * c->stage_cols);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->d_edges, edges, sizeof(double) * (n_bins + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_one, &one, sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     qsgw_chi0_destroy(c);
     *ctx = nullptr;
-    return cuda_status(e);
+    return e == cudaErrorMemoryAllocation ? QSGW_ERR_NOMEM : cuda_status(e);
   }
   return QSGW_OK;
 }
@@ -570,33 +640,40 @@ qsgw_status qsgw_spectral_accumulate(qsgw_ctx* c, const void* Z, long long ldz, 
   QSGW_CK(cudaStreamSynchronize(c->stream));
   const int n_in = off[c->n_bins];
   if (n_in == 0) return QSGW_OK;
-  st = grow(&c->d_zsort, &c->zsort_cap, sizeof(double2) * (size_t)n_pb * n_in);
-  if (st != QSGW_OK) return st;
-  double2* Zs = static_cast<double2*>(c->d_zsort);
-  launch_gather_cols(static_cast<const double2*>(Z), ldz, n_pb, static_cast<const int*>(c->d_perm), n_in, Zs,
-                     c->stream);
-  // every non-empty bin is a block of columns with weight 1 (n_occ = count, n_unocc = 1)
-  MixedBlock mb[32];
-  int nb = 0;
+  // bins whose staging cannot take this call's columns are flushed first (stream order puts the
+  // flush's reads of the staging before the gather's writes); a bin with more columns than the
+  // staging holds takes them through the overflow buffer and is updated at once
+  const int cap = c->stage_cols;
+  std::vector<int> fl;
+  bool over = false;
   for (int j = 0; j < c->n_bins; ++j) {
     const int cnt = off[j + 1] - off[j];
-    if (cnt == 0) continue;
-    const QAcc& a = c->q[j];
-    const double2* Zj = Zs + (size_t)off[j] * n_pb;
-    if (c->prec == QSGW_FP64) {
-      st = accumulate_device(c, j, Zj, false, n_pb, cnt, 1, nullptr, nullptr, c->d_one);
-      if (st != QSGW_OK) return st;
-      continue;
-    }
-    mb[nb++] = MixedBlock{Zj, n_pb, a.n_pb, a.n_pad, cnt, 1, nullptr, nullptr, static_cast<float4*>(a.acc), false,
-                          c->d_one};
-    if (nb == 32) {
-      st = mixed_accumulate_batch(c->mixed, nb, mb, c->g, c->d_err, c->stream);
-      if (st != QSGW_OK) return st;
-      nb = 0;
+    if (cnt > 0 && c->fill[j] > 0 && c->fill[j] + cnt > cap) fl.push_back(j);
+    over = over || cnt > cap;
+  }
+  st = spectral_flush(c, fl);
+  if (st != QSGW_OK) return st;
+  const size_t cb = spectral_col_bytes(c);
+  if (over && (st = grow(&c->d_zsort, &c->zsort_cap, cb * (size_t)n_in)) != QSGW_OK) return st;
+  std::vector<BinCols> direct;
+  for (int j = 0; j < c->n_bins; ++j) {
+    const int cnt = off[j + 1] - off[j];
+    if (cnt > cap) {
+      c->h_dptr[j] = static_cast<uint8_t*>(c->d_zsort) + (size_t)off[j] * cb;
+      direct.push_back({j, c->h_dptr[j], cnt});
+    } else {
+      c->h_dptr[j] = static_cast<uint8_t*>(c->d_stage) + ((size_t)j * cap + c->fill[j]) * cb;
     }
   }
-  if (nb > 0) st = mixed_accumulate_batch(c->mixed, nb, mb, c->g, c->d_err, c->stream);
+  QSGW_CK(cudaMemcpyAsync(c->d_dptr, c->h_dptr.data(), sizeof(void*) * c->n_bins, cudaMemcpyHostToDevice, c->stream));
+  launch_gather_bins(static_cast<const double2*>(Z), ldz, n_pb, static_cast<const int*>(c->d_perm),
+                     static_cast<const int*>(c->d_bins), c->d_offsets, n_in, c->d_dptr, c->prec != QSGW_FP64,
+                     c->stream);
+  for (int j = 0; j < c->n_bins; ++j) {
+    const int cnt = off[j + 1] - off[j];
+    if (cnt <= cap) c->fill[j] += cnt;
+  }
+  st = spectral_update(c, direct);
   if (st != QSGW_OK) return st;
   return cuda_status(cudaGetLastError());
 }
@@ -604,6 +681,10 @@ qsgw_status qsgw_spectral_accumulate(qsgw_ctx* c, const void* Z, long long ldz, 
 qsgw_status qsgw_spectral_finalize(qsgw_ctx* c, void* S) {
   if (!c || !S) return QSGW_ERR_ARG;
   if (!c->spectral) return QSGW_ERR_STATE;
+  std::vector<int> all(c->n_bins);
+  for (int j = 0; j < c->n_bins; ++j) all[j] = j;
+  qsgw_status st = spectral_flush(c, all);  // the staged columns enter S_j
+  if (st != QSGW_OK) return st;
   const size_t nn = (size_t)c->q[0].n_pb * c->q[0].n_pb;
   for (int j = 0; j < c->n_bins; ++j) {
     const QAcc& a = c->q[j];

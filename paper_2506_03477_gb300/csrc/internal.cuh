@@ -53,8 +53,10 @@ void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, cu
 // ([n_bins + 1]) and the stable permutation perm (columns in bin order; offsets[n_bins] of them).
 void launch_hist_sort(const double* eo, const double* eu, int n_occ, int n_unocc, const double* edges, int n_bins,
                       int* bins, int* counts, int* offsets, int* perm, int* d_err, cudaStream_t s);
-void launch_gather_cols(const double2* Z, long long ldz, int n_pb, const int* perm, int n, double2* Zs,
-                        cudaStream_t s);
+// Sorted column p (p < n) -> column p - offsets[j] of dptr[j] (device array of n_bins device
+// pointers), j its bin; complex64 destinations (z32) or complex128.
+void launch_gather_bins(const double2* Z, long long ldz, int n_pb, const int* perm, const int* bins,
+                        const int* offsets, int n, void* const* dptr, bool z32, cudaStream_t s);
 // out[o] += i * coef[o] * S[bins_out[o]] (nn complex elements each).
 void launch_add_antiherm(const double2* S, long long nn, int n_out, const int* bins_out, const double* coef,
                          double2* out, cudaStream_t s);

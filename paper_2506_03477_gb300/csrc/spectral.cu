@@ -1,7 +1,8 @@
 // Real-axis route of chi0 (Eqs. (impolf) and (hilbert), Sec. 2): the transition columns are put
 // in the histogram bins [edges[j], edges[j+1]) holding their energy Delta, gathered bin by bin
-// (pair compaction), and each bin's spectral weight S_j = sum_{r in bin j} conj(z_I,r) z_J,r is a
-// Hermitian update run by the chi0 kernels with weight 1. The kernels here do the binning, a
+// (pair compaction) into per-bin staging that collects the columns of many accumulate calls, and
+// each bin's spectral weight S_j = sum_{r in bin j} conj(z_I,r) z_J,r is a Hermitian update run by
+// the chi0 kernels with weight 1 over the staged columns. The kernels here do the binning, a
 // stable counting sort of the columns by bin, the gather, and the anti-Hermitian part of the
 // real-axis chi0 after the Hilbert transformation. Every step is deterministic.
 #include "internal.cuh"
@@ -82,13 +83,23 @@ __global__ void __launch_bounds__(1024) hist_perm_kernel(const int* __restrict__
   }
 }
 
-// Zs[:, p] = Z[:, perm[p]] for p < n (columns of n_pb complex values; one CTA per column).
-__global__ void __launch_bounds__(256) gather_cols_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
-                                                          const int* __restrict__ perm, double2* __restrict__ Zs) {
-  const long long p = blockIdx.x;
-  const double2* src = Z + (long long)perm[p] * ldz;
-  double2* dst = Zs + p * n_pb;
-  for (int i = threadIdx.x; i < n_pb; i += 256) dst[i] = src[i];
+__device__ __forceinline__ void put(double2* d, double2 x) { *d = x; }
+__device__ __forceinline__ void put(float2* d, double2 x) { *d = make_float2((float)x.x, (float)x.y); }
+
+// Column p of the sorted order, Z[:, perm[p]] in bin j = bins[perm[p]], goes to column
+// p - offsets[j] of that bin's destination dptr[j] (n_pb complex values per column; one CTA per
+// column). complex64 destinations take Z rounded to nearest, the rounding the digit preparation
+// applies to complex128 input, so staging in complex64 leaves the mixed-precision result unchanged.
+template <typename T>
+__global__ void __launch_bounds__(256) gather_bins_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
+                                                          const int* __restrict__ perm, const int* __restrict__ bins,
+                                                          const int* __restrict__ offsets, T* const* __restrict__ dptr) {
+  const int p = blockIdx.x;
+  const int r = perm[p];
+  const int j = bins[r];
+  const double2* src = Z + (long long)r * ldz;
+  T* dst = dptr[j] + (long long)(p - offsets[j]) * n_pb;
+  for (int i = threadIdx.x; i < n_pb; i += 256) put(dst + i, src[i]);
 }
 
 // out[o] += i * coef[o] * S[bins_out[o]] (element-wise, complex), for the anti-Hermitian part of
@@ -120,9 +131,15 @@ void launch_hist_sort(const double* eo, const double* eu, int n_occ, int n_unocc
   hist_perm_kernel<<<n_bins, 1024, 0, s>>>(bins, K, offsets, perm);
 }
 
-void launch_gather_cols(const double2* Z, long long ldz, int n_pb, const int* perm, int n, double2* Zs,
-                        cudaStream_t s) {
-  if (n > 0) gather_cols_kernel<<<n, 256, 0, s>>>(Z, ldz, n_pb, perm, Zs);
+void launch_gather_bins(const double2* Z, long long ldz, int n_pb, const int* perm, const int* bins,
+                        const int* offsets, int n, void* const* dptr, bool z32, cudaStream_t s) {
+  if (n <= 0) return;
+  if (z32)
+    gather_bins_kernel<float2><<<n, 256, 0, s>>>(Z, ldz, n_pb, perm, bins, offsets,
+                                                 reinterpret_cast<float2* const*>(dptr));
+  else
+    gather_bins_kernel<double2><<<n, 256, 0, s>>>(Z, ldz, n_pb, perm, bins, offsets,
+                                                  reinterpret_cast<double2* const*>(dptr));
 }
 
 void launch_add_antiherm(const double2* S, long long nn, int n_out, const int* bins_out, const double* coef,
