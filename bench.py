@@ -499,10 +499,24 @@ def run_realaxis(args):
     N.qsgw_chi0_destroy(ctx)
     acc_ms, fin_ms, re_ms = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]))
     flops = 4.0 * nk * ncol * N_PB * (N_PB + 1)  # every column enters exactly one bin
+    # the FP64 form on 2 of the k-points (the FP64 HERK runs near 1 TFLOP/s)
+    k64 = min(2, nk)
+    ctx64 = N.qsgw_spectral_init(N_PB, edges, N.QSGW_FP64, stream=stream)
+    e64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e64[0].record(stream)
+    for k in range(k64):
+        N.qsgw_spectral_accumulate(ctx64, Z[k], N_PB, N_OCC, N_UNOCC, eo[k], eu[k])
+    N.qsgw_spectral_finalize(ctx64, S)
+    e64[1].record(stream)
+    torch.cuda.synchronize(dev)
+    N.qsgw_chi0_destroy(ctx64)
+    fp64_tflops = 4.0 * k64 * ncol * N_PB * (N_PB + 1) / (e64[0].elapsed_time(e64[1]) * 1e-3) / 1e12
     out = {"metric": "real-axis chi0 (Eqs. impolf, hilbert): algorithmic TFLOP/s of the spectral weights S_j",
            "workload": f"medium n_pb={N_PB}, {nk} k x {ncol} columns, {nb} log bins, 12 real-axis outputs",
            "value": flops / ((acc_ms + fin_ms) * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_accumulate": acc_ms,
            "ms_finalize": fin_ms, "ms_real_axis": re_ms, "flops": flops, "clocks": clk.summary(),
+           "fp64": {"value": fp64_tflops, "unit": "TFLOP/s", "sample": f"{k64} of {nk} k-points, all bins"},
+           "mixed_over_fp64": flops / ((acc_ms + fin_ms) * 1e-3) / 1e12 / fp64_tflops,
            "note": "value counts the accumulate calls and the finalize (the flush of the last staged columns "
                    "and the readout of all S_j); per k-point: bin + stable counting sort + gather into per-bin "
                    "staging; bins are updated 32 per launch when their staging fills"}
