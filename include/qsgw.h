@@ -227,8 +227,9 @@ qsgw_status qsgw_spectral_finalize(qsgw_ctx *ctx, void *S);
 /* chi0 on the real axis (without s) at the centres w_o of the bins bins_out[o] (host [n_out],
  * each in [0, n_bins)), from S as written by qsgw_spectral_finalize (device):
  *   out[o] = sum_j K_j(w_o) S_j + i (-pi / (R - L)) S_{bins_out[o]},
- * device complex128 [n_out][n_pb][n_pb]. The Hilbert sum is a library GEMM (cuBLAS DGEMM over the
- * bins); the anti-Hermitian part is added by a kernel. Synchronises. */
+ * device complex128 [n_out][n_pb][n_pb]. One FP64 kernel sums the bins in increasing j for every
+ * element on or above the diagonal, adds the anti-Hermitian part and writes the mirror (S_j must
+ * be exactly Hermitian, as qsgw_spectral_finalize writes it). Synchronises. */
 qsgw_status qsgw_spectral_real_axis(qsgw_ctx *ctx, const void *S, int n_out, const int *bins_out, void *out);
 
 /* ---- diagnostics (no counterpart in the paper) ---------------------------------------------

@@ -1,6 +1,5 @@
 // C ABI (include/qsgw.h): context, argument validation, host staging, stream ordering, and
 // the eps^{-1} step through cuSOLVER (FP64 Cholesky: potrf + potri, one stream per frequency).
-#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -60,7 +59,6 @@ struct qsgw_ctx {
   std::vector<int> fill;       // columns staged per bin
   void** d_dptr = nullptr;     // [n_bins] gather destinations of one call
   std::vector<void*> h_dptr;
-  cublasHandle_t blas = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<QAcc> q;
   int* d_err = nullptr;
@@ -555,7 +553,6 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   for (void* p : {(void*)c->d_edges, (void*)c->d_one, (void*)c->d_offsets, (void*)c->d_counts, c->d_bins, c->d_perm,
                   c->d_zsort, c->d_stage, (void*)c->d_dptr})
     if (p) cudaFree(p);
-  if (c->blas) cublasDestroy(c->blas);
   if (c->cstream) cudaStreamSynchronize(c->cstream);
   for (int i = 0; i < 2; ++i) {
     if (c->d_hstage[i]) cudaFree(c->d_hstage[i]);
@@ -702,7 +699,6 @@ qsgw_status qsgw_spectral_real_axis(qsgw_ctx* c, const void* S, int n_out, const
   for (int o = 0; o < n_out; ++o)
     if (bins_out[o] < 0 || bins_out[o] >= nb) return QSGW_ERR_ARG;
   const int n_pb = c->q[0].n_pb;
-  const long long nn = (long long)n_pb * n_pb;
   // Hilbert weights of every bin at the output frequencies (bin centres), FP64 on the host:
   // (1/(R-L)) P.V. int_L^R [1/(w-D) - 1/(w+D)] dD for a density uniform in the bin
   std::vector<double> Kw((size_t)n_out * nb), coef(n_out);
@@ -724,19 +720,9 @@ qsgw_status qsgw_spectral_real_axis(qsgw_ctx* c, const void* S, int n_out, const
   if (e == cudaSuccess) e = cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * n_out, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dbins, bins_out, sizeof(int) * n_out, cudaMemcpyHostToDevice, c->stream);
   qsgw_status st = cuda_status(e);
-  if (st == QSGW_OK && !c->blas && cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) st = QSGW_ERR_CUDA;
-  if (st == QSGW_OK && cublasSetStream(c->blas, c->stream) != CUBLAS_STATUS_SUCCESS) st = QSGW_ERR_CUDA;
-  if (st == QSGW_OK) {
-    // Hermitian part, Eq. (hilbert): out (2nn x n_out) = S (2nn x n_bins) * K^T, re and im parts alike
-    const double one = 1.0, zero = 0.0;
-    if (cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)(2 * nn), n_out, nb, &one,
-                    static_cast<const double*>(S), (int)(2 * nn), dK, n_out, &zero, static_cast<double*>(out),
-                    (int)(2 * nn)) != CUBLAS_STATUS_SUCCESS)
-      st = QSGW_ERR_CUDA;
-  }
-  if (st == QSGW_OK) {  // anti-Hermitian part, Eq. (impolf): -pi S_i / (R_i - L_i)
-    launch_add_antiherm(static_cast<const double2*>(S), nn, n_out, dbins, dcoef, static_cast<double2*>(out),
-                        c->stream);
+  if (st == QSGW_OK) {  // Hilbert sum and anti-Hermitian part in one kernel
+    launch_hilbert(static_cast<const double2*>(S), n_pb, nb, n_out, dK, dbins, dcoef, static_cast<double2*>(out),
+                   c->stream);
     st = cuda_status(cudaGetLastError());
   }
   if (st == QSGW_OK) st = cuda_status(cudaStreamSynchronize(c->stream));

@@ -57,9 +57,10 @@ void launch_hist_sort(const double* eo, const double* eu, int n_occ, int n_unocc
 // pointers), j its bin; complex64 destinations (z32) or complex128.
 void launch_gather_bins(const double2* Z, long long ldz, int n_pb, const int* perm, const int* bins,
                         const int* offsets, int n, void* const* dptr, bool z32, cudaStream_t s);
-// out[o] += i * coef[o] * S[bins_out[o]] (nn complex elements each).
-void launch_add_antiherm(const double2* S, long long nn, int n_out, const int* bins_out, const double* coef,
-                         double2* out, cudaStream_t s);
+// out[o] = sum_j K[j * n_out + o] S_j + i coef[o] S_{bins_out[o]} for o < n_out (device arrays;
+// S [nb][n][n] exactly Hermitian, out [n_out][n][n], column-major complex128).
+void launch_hilbert(const double2* S, int n, int nb, int n_out, const double* K, const int* bins_out,
+                    const double* coef, double2* out, cudaStream_t s);
 
 // ---- synthetic Z (synth.cu)
 void launch_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, int n_occ, int n_unocc, double s_div,

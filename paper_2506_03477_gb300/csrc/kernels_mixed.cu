@@ -28,6 +28,7 @@
 // both accumulators are stashed, and two drainer warps scale them by 2^-(eA+eB) (exact) and add
 // them into a double-float (2 x FP32) accumulator in global memory while the next chunk's MMAs
 // run; GB300's FP64 rate (~1 TFLOP/s) would make an FP64 read-modify-write here the bottleneck.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -115,14 +116,59 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // ------------------------------------------------------------------ prep: columns
-// One CTA per chunk of CHR columns: Delta, domain check, |w_l| in FP32 ([r][l]), and the
-// per-chunk maximum of each |w_l| (for the B-operand scale bound).
+constexpr int kMaxBlocks = 32;  // blocks per launch (descriptors travel by value as kernel parameters)
+
+// Column preparation of one block of a batch: the weights are computed from the levels (eo, eu:
+// Delta, domain check, |w_l| for every frequency) or given (wv: w_r = wv[r mod n_unocc], one set;
+// Eq. (sigx) column r = n' * n_pb + mu carries the Coulomb eigenvalue v_mu(k)).
+struct PrepColsBlk {
+  const double* eo;
+  const double* eu;
+  const double* wv;  // non-null: given weights
+  float* wst;        // [r][l] FP32 weights
+  float* wmax;       // [chunk][l] their chunk maxima (the B-operand scale bound)
+  long long K;
+  int n_unocc, n_ch;
+};
+struct PrepColsArgs {
+  PrepColsBlk b[kMaxBlocks];
+  OmegaGrid g;
+  int* d_err;
+};
+
+// One CTA per (chunk of CHR columns, block); CTAs past a block's chunk count leave at once.
 constexpr int PC_THREADS = 1024;  // prep_cols threads per chunk; each handles CHR / PC_THREADS columns
-__global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const double* __restrict__ eo, const double* __restrict__ eu,
-                                                        int n_unocc, long long K, OmegaGrid g, float* __restrict__ wst,
-                                                        float* __restrict__ wmax, int* d_err) {
+__global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const __grid_constant__ PrepColsArgs p) {
   __shared__ float red[PC_THREADS / 32][kMaxOmega];
-  const int c = blockIdx.x, t = threadIdx.x, L = g.L;
+  const PrepColsBlk& B = p.b[blockIdx.y];
+  const int c = blockIdx.x, t = threadIdx.x;
+  if (c >= B.n_ch) return;
+  const long long K = B.K;
+  if (B.wv) {  // given weights, checked > 0 and finite
+    float wm = 0.f;
+    for (int sub = 0; sub < CHR / PC_THREADS; ++sub) {
+      const long long r = (long long)c * CHR + sub * PC_THREADS + t;
+      float w = 0.f;
+      if (r < K) {
+        const double x = B.wv[r % B.n_unocc];
+        const bool ok = (x > 0.0) && isfinite(x);
+        if (!ok) atomicCAS(p.d_err, DEV_OK, DEV_DOMAIN);
+        w = ok ? (float)x : 0.f;
+      }
+      B.wst[r] = w;
+      wm = fmaxf(wm, w);
+    }
+    for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    if ((t & 31) == 0) red[t >> 5][0] = wm;
+    __syncthreads();
+    if (t == 0) {
+      float m = 0.f;
+      for (int w = 0; w < PC_THREADS / 32; ++w) m = fmaxf(m, red[w][0]);
+      B.wmax[c] = m;
+    }
+    return;
+  }
+  const int L = p.g.L;
   float wm[kMaxOmega];  // loops over l run to the constant kMaxOmega so wm stays in registers
 #pragma unroll
   for (int l = 0; l < kMaxOmega; ++l) wm[l] = 0.f;
@@ -131,17 +177,17 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const double* __r
     bool ok = false;
     float d = 0.f;
     if (r < K) {
-      const int n = (int)(r / n_unocc), m = (int)(r % n_unocc);
-      const double dd = eu[m] - eo[n];
+      const int n = (int)(r / B.n_unocc), m = (int)(r % B.n_unocc);
+      const double dd = B.eu[m] - B.eo[n];
       ok = (dd > 0.0) && isfinite(dd);
-      if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
+      if (!ok) atomicCAS(p.d_err, DEV_OK, DEV_DOMAIN);
       d = (float)dd;
     }
 #pragma unroll
     for (int l = 0; l < kMaxOmega; ++l) {
       if (l >= L) break;
-      const float w = ok ? 2.f * d / (d * d + g.w2f[l]) : 0.f;
-      wst[r * L + l] = w;
+      const float w = ok ? 2.f * d / (d * d + p.g.w2f[l]) : 0.f;
+      B.wst[r * L + l] = w;
       wm[l] = fmaxf(wm[l], w);
     }
   }
@@ -156,38 +202,7 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const double* __r
   if (t < L) {
     float m = 0.f;
     for (int w = 0; w < PC_THREADS / 32; ++w) m = fmaxf(m, red[w][t]);
-    wmax[c * L + t] = m;
-  }
-}
-
-// Given weights (one set, L = 1): w_r = wv[r mod period] in FP32, checked > 0 and finite, and the
-// per-chunk maximum. One CTA per chunk of CHR columns. (Eq. (sigx): column r = n' * n_pb + mu
-// carries the Coulomb eigenvalue v_mu(k).)
-__global__ void __launch_bounds__(PC_THREADS) prep_cols_given_kernel(const double* __restrict__ wv, int period,
-                                                                     long long K, float* __restrict__ wst,
-                                                                     float* __restrict__ wmax, int* d_err) {
-  __shared__ float red[PC_THREADS / 32];
-  const int c = blockIdx.x, t = threadIdx.x;
-  float wm = 0.f;
-  for (int sub = 0; sub < CHR / PC_THREADS; ++sub) {
-    const long long r = (long long)c * CHR + sub * PC_THREADS + t;
-    float w = 0.f;
-    if (r < K) {
-      const double x = wv[r % period];
-      const bool ok = (x > 0.0) && isfinite(x);
-      if (!ok) atomicCAS(d_err, DEV_OK, DEV_DOMAIN);
-      w = ok ? (float)x : 0.f;
-    }
-    wst[r] = w;
-    wm = fmaxf(wm, w);
-  }
-  for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
-  if ((t & 31) == 0) red[t >> 5] = wm;
-  __syncthreads();
-  if (t == 0) {
-    float m = 0.f;
-    for (int w = 0; w < PC_THREADS / 32; ++w) m = fmaxf(m, red[w]);
-    wmax[c] = m;
+    B.wmax[c * L + t] = m;
   }
 }
 
@@ -197,13 +212,35 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_given_kernel(const doubl
 // ([plane][k-group 4][row-group 16][8 rows][8 K'] BF16, canonical no-swizzle K-major), and the
 // FP32 copy of Z laid out per J-tile and K-block ([jt][kb][16 r][TJ] float2) for the B side.
 // TZ: double2 (complex128 input) or float2 (complex64): every element is rounded to FP32 on load.
+// All blocks of one launch have the same TZ; grid (chunk, row tile, block), CTAs past a block's
+// chunk or row-tile count leave at once.
+struct PrepRowsBlk {
+  const void* Z;  // TZ [r][ldz]
+  long long ldz, K;
+  uint8_t* aplanes;
+  float2* braw;
+  float* zmax;
+  int* expA;
+  int n_pb, n_pad, n_kb, n_jt, n_ch, n_it;
+};
+struct PrepRowsArgs {
+  PrepRowsBlk b[kMaxBlocks];
+  int TJ;
+};
+
 template <typename TZ>
-__global__ void __launch_bounds__(256) prep_rows_kernel(const TZ* __restrict__ Z, long long ldz, int n_pb,
-                                                        long long K, int n_pad, int n_kb, int TJ, int n_jt,
-                                                        uint8_t* __restrict__ aplanes, float2* __restrict__ braw,
-                                                        float* __restrict__ zmax, int* __restrict__ expA) {
+__global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ PrepRowsArgs p) {
   __shared__ float red[4][TI];
+  const PrepRowsBlk& B = p.b[blockIdx.z];
   const int c = blockIdx.x, it = blockIdx.y;
+  if (c >= B.n_ch || it >= B.n_it) return;
+  const TZ* __restrict__ Z = static_cast<const TZ*>(B.Z);
+  const long long ldz = B.ldz, K = B.K;
+  const int n_pb = B.n_pb, n_pad = B.n_pad, n_kb = B.n_kb, n_jt = B.n_jt, TJ = p.TJ;
+  uint8_t* __restrict__ aplanes = B.aplanes;
+  float2* __restrict__ braw = B.braw;
+  float* __restrict__ zmax = B.zmax;
+  int* __restrict__ expA = B.expA;
   const int il = threadIdx.x & (TI - 1), q = threadIdx.x >> 6;
   const int I = it * TI + il;
   const bool rowok = I < n_pb;
@@ -279,7 +316,6 @@ struct BlockDesc {
   int n_pb, n_pad, n_kb, n_tiles, n_ch;
   int n_kbr;      // K-blocks holding columns (ceil(K / KBR)); the rest of the last chunk is padding
 };
-constexpr int kMaxBlocks = 32;  // blocks per launch (descriptors travel by value as kernel parameters)
 constexpr int kFscrPerCta = 256 * 128;  // flush scratch pairs per CTA: [column n < 256][accumulator lane < 128]
 
 // Work schedule. The T tiles of all blocks (block-major, then tile-major, so consecutive tiles share
@@ -897,6 +933,15 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   a.fscr = reinterpret_cast<float2*>(base);
   a.pbuf = reinterpret_cast<float2*>(base + fscr_bytes);
   int T = 0, min_ch_tail = 1 << 30;
+  // one column-preparation launch for the batch, one row-preparation launch per Z element type
+  PrepColsArgs pc;
+  std::memset(&pc, 0, sizeof(pc));
+  pc.g = g;
+  pc.d_err = d_err;
+  PrepRowsArgs pr[2];  // [0]: complex128 Z, [1]: complex64
+  std::memset(pr, 0, sizeof(pr));
+  pr[0].TJ = pr[1].TJ = TJ;
+  int nr[2] = {0, 0}, max_it[2] = {0, 0}, max_chr[2] = {0, 0}, max_ch = 0;
   for (int b = 0; b < nb; ++b) {
     const Plan& P = pl[b];
     const MixedBlock& B = in[b];
@@ -918,23 +963,19 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     d.n_kbr = (int)((P.K + KBR - 1) / KBR);
     d.n_ch = P.n_ch;
     T += d.n_tiles;
-    if (B.wv)
-      prep_cols_given_kernel<<<P.n_ch, PC_THREADS, 0, stream>>>(B.wv, B.n_unocc, P.K, const_cast<float*>(d.wst),
-                                                                const_cast<float*>(d.wmax), d_err);
-    else
-      prep_cols_kernel<<<P.n_ch, PC_THREADS, 0, stream>>>(B.eo, B.eu, B.n_unocc, P.K, g, const_cast<float*>(d.wst),
-                                                          const_cast<float*>(d.wmax), d_err);
-    if (B.z32)
-      prep_rows_kernel<float2><<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(
-          static_cast<const float2*>(B.Z), B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
-          const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw), const_cast<float*>(d.zmax),
-          const_cast<int*>(d.expA));
-    else
-      prep_rows_kernel<double2><<<dim3(P.n_ch, P.n_it), 256, 0, stream>>>(
-          static_cast<const double2*>(B.Z), B.ldz, B.n_pb, P.K, B.n_pad, P.n_kb, TJ, P.n_jt,
-          const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw), const_cast<float*>(d.zmax),
-          const_cast<int*>(d.expA));
+    pc.b[b] = PrepColsBlk{B.eo, B.eu, B.wv, reinterpret_cast<float*>(base + P.o_w),
+                          reinterpret_cast<float*>(base + P.o_wmax), P.K, B.n_unocc, P.n_ch};
+    const int t = B.z32 ? 1 : 0;
+    pr[t].b[nr[t]++] = PrepRowsBlk{B.Z, B.ldz, P.K, base + P.o_a, reinterpret_cast<float2*>(base + P.o_raw),
+                                   reinterpret_cast<float*>(base + P.o_zmax), reinterpret_cast<int*>(base + P.o_exp),
+                                   B.n_pb, B.n_pad, P.n_kb, P.n_jt, P.n_ch, P.n_it};
+    max_ch = std::max(max_ch, P.n_ch);
+    max_chr[t] = std::max(max_chr[t], P.n_ch);
+    max_it[t] = std::max(max_it[t], P.n_it);
   }
+  prep_cols_kernel<<<dim3(max_ch, nb), PC_THREADS, 0, stream>>>(pc);
+  if (nr[0] > 0) prep_rows_kernel<double2><<<dim3(max_chr[0], max_it[0], nr[0]), 256, 0, stream>>>(pr[0]);
+  if (nr[1] > 0) prep_rows_kernel<float2><<<dim3(max_chr[1], max_it[1], nr[1]), 256, 0, stream>>>(pr[1]);
   // whole tiles first; the last R tiles (a partial last wave) are split into P chunk ranges
   const int G = s.n_sm;
   const int R = T >= G ? T % G : T;
@@ -1062,11 +1103,20 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   d.n_kbr = (int)((K + KBR - 1) / KBR);
   d.n_tiles = n_tiles;
   d.n_ch = n_ch;
-  prep_cols_kernel<<<n_ch, PC_THREADS, 0, stream>>>(eo, eu, n_unocc, K, g, const_cast<float*>(d.wst),
-                                            const_cast<float*>(d.wmax), d_err);
-  prep_rows_kernel<double2><<<dim3(n_ch, n_it), 256, 0, stream>>>(Z, ldz, n_pb, K, n_pad, n_kb, TJ, n_jt,
-                                                          const_cast<uint8_t*>(d.aplanes), const_cast<float2*>(d.braw),
-                                                          const_cast<float*>(d.zmax), const_cast<int*>(d.expA));
+  PrepColsArgs pc;
+  std::memset(&pc, 0, sizeof(pc));
+  pc.g = g;
+  pc.d_err = d_err;
+  pc.b[0] = PrepColsBlk{eo, eu, nullptr, reinterpret_cast<float*>(base + o_w), reinterpret_cast<float*>(base + o_wmax),
+                        K, n_unocc, n_ch};
+  prep_cols_kernel<<<dim3(n_ch, 1), PC_THREADS, 0, stream>>>(pc);
+  PrepRowsArgs pr;
+  std::memset(&pr, 0, sizeof(pr));
+  pr.TJ = TJ;
+  pr.b[0] = PrepRowsBlk{Z, ldz, K, base + o_a, reinterpret_cast<float2*>(base + o_raw),
+                        reinterpret_cast<float*>(base + o_zmax), reinterpret_cast<int*>(base + o_exp),
+                        n_pb, n_pad, n_kb, n_jt, n_ch, n_it};
+  prep_rows_kernel<double2><<<dim3(n_ch, n_it, 1), 256, 0, stream>>>(pr);
   a.fscr = reinterpret_cast<float2*>(base + o_fscr);
   a.pbuf = reinterpret_cast<float2*>(base + o_fscr + (size_t)cap_ctas * fscr_cta);
   const int G = n_sm < cap_ctas ? n_sm : cap_ctas, T = n_tiles;

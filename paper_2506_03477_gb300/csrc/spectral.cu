@@ -3,8 +3,8 @@
 // (pair compaction) into per-bin staging that collects the columns of many accumulate calls, and
 // each bin's spectral weight S_j = sum_{r in bin j} conj(z_I,r) z_J,r is a Hermitian update run by
 // the chi0 kernels with weight 1 over the staged columns. The kernels here do the binning, a
-// stable counting sort of the columns by bin, the gather, and the anti-Hermitian part of the
-// real-axis chi0 after the Hilbert transformation. Every step is deterministic.
+// stable counting sort of the columns by bin, the gather, and the real-axis chi0 (the Hilbert
+// transformation and the anti-Hermitian part). Every step is deterministic.
 #include "internal.cuh"
 
 namespace qsgw {
@@ -102,21 +102,59 @@ __global__ void __launch_bounds__(256) gather_bins_kernel(const double2* __restr
   for (int i = threadIdx.x; i < n_pb; i += 256) put(dst + i, src[i]);
 }
 
-// out[o] += i * coef[o] * S[bins_out[o]] (element-wise, complex), for the anti-Hermitian part of
-// the real-axis chi0: -pi S_i / (R_i - L_i) times i.
-__global__ void add_antiherm_kernel(const double2* __restrict__ S, long long nn, int n_out,
-                                    const int* __restrict__ bins_out, const double* __restrict__ coef,
-                                    double2* __restrict__ out) {
-  const int o = blockIdx.y;
-  const double2* s = S + (long long)bins_out[o] * nn;
-  double2* d = out + (long long)o * nn;
-  const double c = coef[o];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
-    const double2 x = s[e];
-    double2 y = d[e];
-    y.x -= c * x.y;
-    y.y += c * x.x;
-    d[e] = y;
+// Real-axis chi0 from the spectral weights (Eqs. (hilbert) and (impolf)), for NO outputs
+// o0 .. o0 + NO - 1 (those below n_out):
+//   out[o] = sum_j K[j][o] S_j + i coef[o] S_{bins_out[o]},
+// the first sum being the Hilbert transformation of the histogram and the second term the
+// anti-Hermitian part inside the output's own bin. S_j is exactly Hermitian (the readout writes
+// the mirror of its upper triangle), so the Hermitian part H_o is too: each thread computes one
+// element on or above the diagonal and writes its mirror, out_JI = conj(H_IJ) + i coef conj(S_IJ).
+// The bins are summed in increasing j in FP64. Block (32, 8): 32 rows I by 8 columns J; grid
+// (row tiles, column groups, output groups); blocks wholly below the diagonal leave at once.
+constexpr int kHilbChunk = 128;  // bins of K staged in shared memory at a time
+
+template <int NO>
+__global__ void __launch_bounds__(256) hilbert_kernel(const double2* __restrict__ S, int n, int nb, int n_out,
+                                                      const double* __restrict__ K, const int* __restrict__ bins_out,
+                                                      const double* __restrict__ coef, double2* __restrict__ out) {
+  __shared__ double sK[kHilbChunk][NO];
+  if (blockIdx.x * 32 > blockIdx.y * 8 + 7) return;
+  const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y;
+  const int tid = threadIdx.y * 32 + threadIdx.x, o0 = blockIdx.z * NO;
+  const bool act = I <= J && J < n;
+  const long long nn = (long long)n * n, e = (long long)J * n + I;
+  double hr[NO], hi[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) hr[o] = hi[o] = 0.0;
+  for (int j0 = 0; j0 < nb; j0 += kHilbChunk) {
+    const int cnt = min(kHilbChunk, nb - j0);
+    __syncthreads();
+    for (int t = tid; t < cnt * NO; t += 256) {
+      const int jj = t / NO, oo = t % NO;
+      sK[jj][oo] = o0 + oo < n_out ? K[(long long)(j0 + jj) * n_out + o0 + oo] : 0.0;
+    }
+    __syncthreads();
+    if (act) {
+      const double2* sp = S + (long long)j0 * nn + e;
+      for (int jj = 0; jj < cnt; ++jj) {
+        const double2 v = sp[jj * nn];
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          hr[o] = fma(sK[jj][o], v.x, hr[o]);
+          hi[o] = fma(sK[jj][o], v.y, hi[o]);
+        }
+      }
+    }
+  }
+  if (!act) return;
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    if (o0 + o >= n_out) break;
+    const double c = coef[o0 + o];
+    const double2 sb = S[(long long)bins_out[o0 + o] * nn + e];
+    double2* dst = out + (long long)(o0 + o) * nn;
+    dst[e] = make_double2(hr[o] - c * sb.y, hi[o] + c * sb.x);
+    if (I != J) dst[(long long)I * n + J] = make_double2(hr[o] + c * sb.y, c * sb.x - hi[o]);
   }
 }
 
@@ -142,11 +180,18 @@ void launch_gather_bins(const double2* Z, long long ldz, int n_pb, const int* pe
                                                   reinterpret_cast<double2* const*>(dptr));
 }
 
-void launch_add_antiherm(const double2* S, long long nn, int n_out, const int* bins_out, const double* coef,
-                         double2* out, cudaStream_t s) {
-  long long blocks = (nn + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
-  add_antiherm_kernel<<<dim3((unsigned)blocks, n_out), 256, 0, s>>>(S, nn, n_out, bins_out, coef, out);
+void launch_hilbert(const double2* S, int n, int nb, int n_out, const double* K, const int* bins_out,
+                    const double* coef, double2* out, cudaStream_t s) {
+  // output groups of at most 12 (registers), sized evenly and rounded up to a multiple of 4
+  const int groups = (n_out + 11) / 12;
+  const int per = ((n_out + groups - 1) / groups + 3) / 4 * 4;
+  const dim3 grid((n + 31) / 32, (n + 7) / 8, (n_out + per - 1) / per), block(32, 8);
+  if (per == 4)
+    hilbert_kernel<4><<<grid, block, 0, s>>>(S, n, nb, n_out, K, bins_out, coef, out);
+  else if (per == 8)
+    hilbert_kernel<8><<<grid, block, 0, s>>>(S, n, nb, n_out, K, bins_out, coef, out);
+  else
+    hilbert_kernel<12><<<grid, block, 0, s>>>(S, n, nb, n_out, K, bins_out, coef, out);
 }
 
 }  // namespace qsgw

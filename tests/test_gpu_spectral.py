@@ -177,3 +177,15 @@ def test_spectral_reset_drops_staged_columns(N):
     for j in range(4):
         ref = second[j] if j == 2 else both[j]
         assert rel_fro(got[j], ref) <= 1e-6, j
+
+
+@pytest.mark.parametrize("bins_out", [[40], list(range(3, 75, 6)), list(range(2, 79, 6))])
+def test_real_axis_output_groups(N, bins_out):
+    """The real-axis kernel takes outputs in groups of 4, 8 or 12 (one output; 12 in one group;
+    13 as two groups of 8, the last padded), FP64 against the oracle, ragged n_pb = 70."""
+    blocks = _blocks(70, [(5, 130), (3, 61)])
+    ref, _ = _oracle_S(blocks)
+    S, P = _gpu_S(N, N.QSGW_FP64, 70, blocks, bins_out)
+    Pref = oracle.real_axis_chi0(ref, EDGES, bins_out)
+    for o in range(len(bins_out)):
+        assert rel_fro(P[o], Pref[o]) <= 1e-11, (o, rel_fro(P[o], Pref[o]))
