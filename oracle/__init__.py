@@ -1,5 +1,5 @@
-"""FP64 CPU oracle for chi0(q, i omega), eps and W, and the exchange self-energy (ctypes wrapper
-around oracle.c).
+"""FP64 CPU oracle for chi0(q, i omega), eps and W, the exchange self-energy, the real-axis
+route and the imaginary-axis correlation self-energy (ctypes wrapper around oracle.c).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the benchmark's
 CPU-baseline leg. The CUDA library never imports or links it, and the two share no code.
@@ -52,6 +52,10 @@ def _load():
         lib.oracle_hilbert_weight.argtypes = [_c_double, _c_double, _c_double]
         lib.oracle_sigx.restype = None
         lib.oracle_sigx.argtypes = [_c_int, _p, _c_int, _c_int, _c_ll, _p, _p, _p]
+        lib.oracle_sigc_weights.restype = None
+        lib.oracle_sigc_weights.argtypes = [_c_double, _c_int, _p, _p]
+        lib.oracle_sigc.restype = None
+        lib.oracle_sigc.argtypes = [_c_int, _p, _c_int, _c_int, _p, _p, _p, _c_int, _p, _p, _p]
         _lib = lib
     return _lib
 
@@ -137,6 +141,37 @@ def real_axis_chi0(S: np.ndarray, edges: np.ndarray, bins_out) -> np.ndarray:
         re = sum(hilbert_weight(w, e[j], e[j + 1]) * S[j] for j in range(S.shape[0]))
         out.append(re - 1j * np.pi / (e[i + 1] - e[i]) * S[i])
     return np.array(out)
+
+
+def sigc_weights(dE: float, omega: np.ndarray) -> np.ndarray:
+    """Integration weights w_i(dE) of Eq. (sigci): sum_i w_i X(i omega_i) ~= (1/pi) int_0^inf
+    dE/(dE^2+w^2) X(iw) dw, X constant below omega_0, linear between mesh points and decaying as
+    1/w^2 beyond the last (the reading stated in oracle.c)."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    w = np.empty(om.size, dtype=np.float64)
+    _load().oracle_sigc_weights(float(dE), int(om.size), _ptr(om), _ptr(w))
+    return w
+
+
+def sigc(Zcols, e_qp: np.ndarray, e_band, omega: np.ndarray, Wc) -> np.ndarray:
+    """Eq. (sigci): I[n, m] = -sum_{k,n',i} w_i(e_qp[n] - e_band[k][n']) sum_{mu,nu}
+    conj(Z_k[n' n, mu]) Wc_k[i, mu, nu] Z_k[n' m, nu]. Per k: Zcols[k] has shape
+    (n_band * n_qp, n_pb) (row r = n' * n_qp + n), e_band[k] shape (n_band,), Wc[k] shape
+    (L, n_pb, n_pb) indexed [i, mu, nu]."""
+    e_q = np.ascontiguousarray(e_qp, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    n_qp, L = e_q.size, om.size
+    n_pb = Zcols[0].shape[1]
+    nb = np.array([len(e) for e in e_band], dtype=np.int32)
+    for k in range(len(Zcols)):
+        assert Zcols[k].shape == (nb[k] * n_qp, n_pb) and Wc[k].shape == (L, n_pb, n_pb)
+    Z = np.ascontiguousarray(np.concatenate([np.asarray(z, dtype=np.complex128) for z in Zcols]))
+    eb = np.ascontiguousarray(np.concatenate(e_band), dtype=np.float64)
+    W = np.ascontiguousarray(np.concatenate([np.asarray(w, dtype=np.complex128).transpose(0, 2, 1) for w in Wc]))
+    out = np.empty((n_qp, n_qp), dtype=np.complex128)  # column-major in C = transposed here
+    _load().oracle_sigc(len(Zcols), _ptr(nb), int(n_pb), int(n_qp), _ptr(Z), _ptr(e_q), _ptr(eb), int(L), _ptr(om),
+                        _ptr(W), _ptr(out))
+    return np.ascontiguousarray(out.T)
 
 
 def eps_w(chi: np.ndarray, v: np.ndarray, want_eps: bool = True, want_wc: bool = True):

@@ -29,8 +29,9 @@
  * l*N*N + j*N + i.
  *
  * Also Eq. (sigx) (exchange self-energy), a Hermitian update of the same form with the
- * Coulomb eigenvalues as column weights: see oracle_sigx; and the real-axis route of Eqs.
- * (impolf) and (hilbert): oracle_hist_spectral, oracle_hilbert_weight.
+ * Coulomb eigenvalues as column weights: see oracle_sigx; the real-axis route of Eqs.
+ * (impolf) and (hilbert): oracle_hist_spectral, oracle_hilbert_weight; and the imaginary-axis
+ * correlation self-energy of Eq. (sigci): oracle_sigc_weights, oracle_sigc.
  */
 #include <complex.h>
 #include <math.h>
@@ -208,4 +209,95 @@ void oracle_eps_w(int N, int L, const zdouble *chi, const double *v, zdouble *ep
       for (int j = 0; j < N; ++j)
         for (int i = 0; i < N; ++i) Wc_out[l * NN + (size_t)j * N + i] = W[(size_t)j * N + i] - (i == j ? v[i] : 0.0);
   }
+}
+
+/* Integration weights of Eq. (sigci), Sec. 2: w[i] such that
+ *   int_{-inf}^{inf} dw/(2 pi) X(i w) / (dE - i w)  ~=  sum_i w[i] X(i omega_i)
+ * for X even in w (W^c(i w) = W^c(-i w)), i.e. (1/pi) int_0^inf dE/(dE^2 + w^2) X(i w) dw.
+ * The paper takes the weights from the method of Aryasetiawan and Gunnarsson, which it cites
+ * but does not give. Reading used here: the sharply peaked factor dE/(dE^2 + w^2) is integrated
+ * exactly and only X is interpolated on the mesh 0 < omega_0 < ... < omega_{L-1}:
+ *   X = X_0 on [0, omega_0];
+ *   X linear between neighbouring mesh points;
+ *   X = X_{L-1} (omega_{L-1} / w)^2 beyond omega_{L-1} (the large-w decay of W^c).
+ * With F(w) = atan(w / dE) and G(w) = (dE / 2) ln(dE^2 + w^2) the antiderivatives of
+ * dE/(dE^2+w^2) and w dE/(dE^2+w^2), segment [a, b] of length h adds (b A - B)/h to the weight of
+ * a and (B - a A)/h to that of b, A = F(b) - F(a), B = G(b) - G(a) (evaluated without
+ * cancellation, see below). The tail adds
+ * (dE / W) T(|dE| / W), W = omega_{L-1}, T(x) = (1 - atan(x)/x) / x^2 (its series for small x).
+ * dE = 0 gives 0 (the principal value of the limits dE -> 0+ and 0-). */
+static double sigc_tail(double x) {
+  if (x < 0.5) {  /* T(x) = sum_k (-1)^k x^(2k) / (2k + 3) */
+    double t = 0.0, p = 1.0;
+    for (int k = 0; k < 40; ++k, p *= -x * x) t += p / (2 * k + 3);
+    return t;
+  }
+  return (1.0 - atan(x) / x) / (x * x);
+}
+
+void oracle_sigc_weights(double dE, int L, const double *omega, double *w) {
+  for (int i = 0; i < L; ++i) w[i] = 0.0;
+  if (dE == 0.0) return;
+  w[0] += atan(omega[0] / dE);
+  for (int i = 0; i + 1 < L; ++i) {
+    const double a = omega[i], b = omega[i + 1], h = b - a;
+    /* A and B as differences of the antiderivatives, in forms without cancellation:
+     * atan(b/dE) - atan(a/dE) = atan(h dE / (dE^2 + a b)) (0 <= a < b), and
+     * ln((dE^2 + b^2) / (dE^2 + a^2)) = log1p((b^2 - a^2) / (dE^2 + a^2)). */
+    const double A = atan(h * dE / (dE * dE + a * b));
+    const double B = 0.5 * dE * log1p((b - a) * (b + a) / (dE * dE + a * a));
+    w[i] += (b * A - B) / h;
+    w[i + 1] += (B - a * A) / h;
+  }
+  const double W = omega[L - 1];
+  w[L - 1] += dE / W * sigc_tail(fabs(dE) / W);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < L; ++i) w[i] /= pi;
+}
+
+/* Eq. (sigci), Sec. 2: the imaginary-axis part of the correlation self-energy,
+ *   I_nm = - sum_k sum_{n'} sum_i w_i(e_qp[n] - e_band[k][n'])
+ *            sum_{mu, nu} conj(Z_k[n' n, mu]) Wc_k(i omega_i)[mu, nu] Z_k[n' m, nu].
+ * Z_k is column-major n_pb x (n_band[k] * n_qp): column r = n' * n_qp + n holds
+ * Z^{(q-k) n', q n}_{k mu} for mu = 0 .. n_pb - 1; the blocks of all k follow one another.
+ * e_band is the concatenation of the n_band[k] band energies e_{q-k, n'}. Wc_k is [L][n_pb][n_pb]
+ * column-major (element (mu, nu) of frequency i at i*n_pb*n_pb + nu*n_pb + mu), blocks of all k
+ * one after another. out is column-major n_qp x n_qp: element (n, m) at m * n_qp + n.
+ * For every (k, n', i) the product y_m = Wc_i Z[n' m, :] is formed first, then its inner
+ * products with conj(Z[n' n, :]). */
+void oracle_sigc(int n_k, const int *n_band, int n_pb, int n_qp, const zdouble *Z, const double *e_qp,
+                 const double *e_band, int L, const double *omega, const zdouble *Wc, zdouble *out) {
+  const size_t nn = (size_t)n_pb * n_pb;
+  for (size_t t = 0; t < (size_t)n_qp * n_qp; ++t) out[t] = 0.0;
+  double *w = (double *)malloc((size_t)n_qp * L * sizeof(double));
+  zdouble *y = (zdouble *)malloc((size_t)n_qp * n_pb * sizeof(zdouble));
+  size_t zoff = 0, eoff = 0;
+  for (int k = 0; k < n_k; ++k) {
+    const zdouble *Wk = Wc + (size_t)k * L * nn;
+    for (int np = 0; np < n_band[k]; ++np) {
+      const zdouble *Zb = Z + zoff + (size_t)np * n_qp * n_pb;  /* column n of this band at Zb + n*n_pb */
+      for (int n = 0; n < n_qp; ++n) oracle_sigc_weights(e_qp[n] - e_band[eoff + np], L, omega, w + (size_t)n * L);
+      for (int i = 0; i < L; ++i) {
+        const zdouble *Wi = Wk + (size_t)i * nn;
+#pragma omp parallel for schedule(static)
+        for (int m = 0; m < n_qp; ++m)
+          for (int mu = 0; mu < n_pb; ++mu) {
+            zdouble t = 0.0;
+            for (int nu = 0; nu < n_pb; ++nu) t += Wi[(size_t)nu * n_pb + mu] * Zb[(size_t)m * n_pb + nu];
+            y[(size_t)m * n_pb + mu] = t;
+          }
+#pragma omp parallel for schedule(static)
+        for (int m = 0; m < n_qp; ++m)
+          for (int n = 0; n < n_qp; ++n) {
+            zdouble t = 0.0;
+            for (int mu = 0; mu < n_pb; ++mu) t += conj(Zb[(size_t)n * n_pb + mu]) * y[(size_t)m * n_pb + mu];
+            out[(size_t)m * n_qp + n] -= w[(size_t)n * L + i] * t;
+          }
+      }
+    }
+    zoff += (size_t)n_band[k] * n_qp * n_pb;
+    eoff += (size_t)n_band[k];
+  }
+  free(w);
+  free(y);
 }
