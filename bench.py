@@ -523,6 +523,91 @@ def run_realaxis(args):
     print(json.dumps(out))
 
 
+def run_sigc(args):
+    """The imaginary-axis correlation self-energy, Eq. (sigci), on the medium shapes. W^c(i omega_l)
+    of one q-point comes from the library's own chain: chi0 of the medium workload (64 k-points),
+    then eps^-1 and W^c (correlation only), 12 frequencies. I^c then runs for 64 target states and
+    256 bands (40 occupied, 216 unoccupied) per k-point over 16 k-points, with Z drawn on the device
+    (complex128, 6.3 GB resident) and the one W^c standing for every k. One step = reset + 16
+    accumulate calls + readout. The FP64 path is timed on 64 bands of one k-point."""
+    import torch
+    from paper_2506_03477_gb300 import native as N
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    n_qp, n_band, n_k = 64, 256, min(16, args.k_points)
+    om = np.asarray(WL.omega, dtype=np.float64)
+    # W^c from chi0 -> eps^-1 -> W^c (set-up, not timed)
+    ctxc = N.qsgw_chi0_init([N_PB], om, WL.spin, N.QSGW_MIXED_BF16X3, stream=stream)
+    tmp = torch.empty((N_OCC * N_UNOCC, N_PB), dtype=torch.complex128, device=dev)
+    for k in range(N_K):
+        eo = torch.from_numpy(eps_occ(WL.seed, 0, k, N_OCC)).to(dev)
+        eu = torch.from_numpy(eps_unocc(WL.seed, 0, k, N_UNOCC)).to(dev)
+        with torch.cuda.stream(stream):
+            N.qsgw_synth_z(WL.seed, 0, k, N_PB, N_OCC, N_UNOCC, WL.s_div, tmp, N_PB, stream=stream)
+        N.qsgw_chi0_accumulate(ctxc, 0, tmp, N_PB, N_OCC, N_UNOCC, eo, eu, om)
+        N.qsgw_chi0_sync(ctxc)
+    del tmp
+    v = torch.from_numpy(coulomb_v(WL.seed, 0, N_PB)).to(dev)
+    Wc = torch.empty((L, N_PB, N_PB), dtype=torch.complex128, device=dev)
+    N.qsgw_eps_inv(ctxc, 0, v, Wc, correlation_only=True, n_omega=L)
+    N.qsgw_chi0_destroy(ctxc)
+    # inputs of I^c
+    rng = np.random.default_rng(WL.seed)
+    e_qp = torch.from_numpy(np.sort(rng.uniform(-0.3, 0.4, n_qp))).to(dev)
+    e_band = [torch.from_numpy(np.concatenate([eps_occ(WL.seed, 1, k, 40), eps_unocc(WL.seed, 1, k, n_band - 40)]))
+              .to(dev) for k in range(n_k)]
+    Zs = torch.empty((n_k, n_band * n_qp, N_PB), dtype=torch.complex128, device=dev)
+    with torch.cuda.stream(stream):
+        for k in range(n_k):
+            N.qsgw_synth_z(WL.seed, 5, k, N_PB, n_band, n_qp, WL.s_div, Zs[k], N_PB, stream=stream)
+    torch.cuda.synchronize(dev)
+    out = torch.empty((n_qp, n_qp), dtype=torch.complex128, device=dev)
+    ctx = N.qsgw_sigc_init(n_qp, N_PB, om, N.QSGW_MIXED_BF16X3, stream=stream)
+
+    def step(nk, c, nb=n_band):
+        N.qsgw_chi0_reset(c, 0)
+        for k in range(nk):
+            N.qsgw_sigc_accumulate(c, Zs[k], N_PB, nb, e_qp, e_band[k], Wc)
+        N.qsgw_sigc_finalize(c, out)
+
+    for _ in range(max(3, args.warmup)):
+        step(n_k, ctx)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(0) as clk:
+        a.record(stream)
+        for _ in range(args.steps):
+            step(n_k, ctx)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / args.steps
+    N.qsgw_chi0_destroy(ctx)
+
+    def flops(nk, nb):  # D = sum_i w_i conj(Z) W^c_i, then D Z^T; 8 real flops per complex MAC
+        return nk * 8.0 * (nb * n_qp * N_PB * L * N_PB + n_qp * n_qp * nb * N_PB)
+
+    ctx64 = N.qsgw_sigc_init(n_qp, N_PB, om, N.QSGW_FP64, stream=stream)
+    step(1, ctx64, 64)  # warm-up
+    a.record(stream)
+    step(1, ctx64, 64)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms64 = a.elapsed_time(b)
+    N.qsgw_chi0_destroy(ctx64)
+    f = flops(n_k, n_band)
+    sustained = peaks()[0]
+    out_d = {"metric": "imaginary-axis correlation self-energy I^c (Eq. sigci): algorithmic TFLOP/s, mixed",
+             "workload": f"sigc n_pb={N_PB}, {L} imaginary frequencies, n_qp={n_qp}, {n_k} k x {n_band} bands; "
+                         "W^c from the medium chi0 -> eps^-1 chain",
+             "value": f / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms, "flops_per_step": f,
+             "fp64": {"value": flops(1, 64) / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "sample": "1 k-point, 64 bands"},
+             "frac_of_bf16_sustained_x8": f / (ms * 1e-3) / 1e12 * 8 / sustained if sustained else None,
+             "clocks": clk.summary(), "steps": args.steps}
+    out_d["mixed_over_fp64"] = out_d["value"] / out_d["fp64"]["value"]
+    print(json.dumps(out_d))
+
+
 # ------------------------------------------------------------------ oracle (CPU) legs
 def oracle_inputs(rows):
     """Rows of Z (host generator) and Delta for the sampled chi0 block."""
@@ -598,11 +683,13 @@ def main():
     ap.add_argument("--sigx-occ", type=int, default=276, help="occupied states per k-point for --workload sigx "
                     "(profiling aid; the workload uses 276)")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batched", "large", "sigx", "realaxis"],
+    ap.add_argument("--workload", default="medium",
+                    choices=["medium", "batched", "large", "sigx", "realaxis", "sigc"],
                     help="medium = the benchmark line; batched = the 24-q uneven workload (q-points/s); "
                          "large = n_pb 4000, 9.2M columns, 16 frequencies (one pass); "
                          "sigx = the exchange self-energy at (InAs)6(GaSb)6 sizes; "
-                         "realaxis = the histogram / Hilbert route on the medium shapes")
+                         "realaxis = the histogram / Hilbert route on the medium shapes; "
+                         "sigc = the imaginary-axis correlation self-energy on the medium shapes")
     ap.add_argument("--k-points", type=int, default=64,
                     help="k-points per step (profiling aid for small captures; bench lines use all 64)")
     args = ap.parse_args()
@@ -643,9 +730,10 @@ def main():
                           "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
-    if args.workload in ("batched", "large", "sigx", "realaxis"):
+    if args.workload in ("batched", "large", "sigx", "realaxis", "sigc"):
         if rank == 0:
-            {"batched": run_batched, "large": run_large, "sigx": run_sigx, "realaxis": run_realaxis}[args.workload](args)
+            {"batched": run_batched, "large": run_large, "sigx": run_sigx, "realaxis": run_realaxis,
+             "sigc": run_sigc}[args.workload](args)
         return
     res = run_ours(args, rank, world, local)
     if rank != 0:

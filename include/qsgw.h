@@ -232,6 +232,46 @@ qsgw_status qsgw_spectral_finalize(qsgw_ctx *ctx, void *S);
  * be exactly Hermitian, as qsgw_spectral_finalize writes it). Synchronises. */
 qsgw_status qsgw_spectral_real_axis(qsgw_ctx *ctx, const void *S, int n_out, const int *bins_out, void *out);
 
+/* ---- imaginary-axis correlation self-energy, Eq. (sigci) (Sec. 2) -------------------------------
+ * The part of the correlation self-energy from the imaginary-axis contour:
+ *   I_nm = - sum_k sum_{n'} sum_i w_i(e_qn - e_{q-k n'})
+ *            sum_{mu, nu} conj(Z_{k, n' n, mu}) W^c_{mu nu}(k, i omega_i) Z_{k, n' m, nu}.
+ * The paper takes the weights w_i from the cited method of Aryasetiawan and Gunnarsson without
+ * stating it. Here dE/(dE^2 + w^2) is integrated exactly against W^c interpolated on the mesh:
+ * constant below omega_0, linear between mesh points, decaying as 1/w^2 beyond the last. The
+ * weights are odd in dE and 0 at dE = 0. Both contractions run on the chi0 kernels as blocks of
+ * Hermitian updates: first D = sum_i w_i conj(Z) W^c_i, then D Z^T. In the mixed precision they
+ * run on the tensor cores; the error is bounded relative to the sum of the terms' magnitudes, as
+ * for chi0.
+ *
+ * Create a context for one q-point:
+ *   n_qp target states, in [1, 4096];
+ *   n_pb in [1, 8192];
+ *   omega: host [n_omega], n_omega <= 16, finite, strictly increasing, omega[0] > 0 (the
+ *     frequencies W^c is given at);
+ *   prec as for qsgw_chi0_init.
+ * qsgw_chi0_reset(ctx, 0) clears the sum; sync / destroy apply; the other chi0 calls return
+ * QSGW_ERR_STATE. */
+qsgw_status qsgw_sigc_init(qsgw_ctx **ctx, int n_qp, int n_pb, int n_omega, const double *omega, qsgw_prec prec,
+                           void *cuda_stream);
+
+/* Add one k-point. All arrays are on the device:
+ *   Z: complex128, column-major n_pb x (n_band * n_qp), leading dimension ldz >= n_pb; column
+ *     r = n' * n_qp + n holds Z^{(q-k) n', q n}_{k mu};
+ *   e_qp: [n_qp], the energies e_qn of the target states (the same in every call);
+ *   e_band: [n_band], the energies e_{q-k n'} of the bands n';
+ *   Wc: complex128 [n_omega][n_pb][n_pb], column-major per frequency, Hermitian, as
+ *     qsgw_eps_inv writes W^c (column mu is read, and W^c_{mu nu} taken as conj(W^c_{nu mu})).
+ * Bands go in batches of 4096 / n_qp. The work is queued on the context's stream, and the inputs
+ * must stay valid until it has run. Non-finite energies set QSGW_ERR_DOMAIN (sticky). */
+qsgw_status qsgw_sigc_accumulate(qsgw_ctx *ctx, const void *Z, long long ldz, int n_band, const double *e_qp,
+                                 const double *e_band, const void *Wc);
+
+/* Write I^c to I: device complex128 n_qp x n_qp, column-major, element (n, m) at m * n_qp + n.
+ * It is not Hermitian in general: the weights depend on the row's energy e_qn. Synchronises and
+ * returns any sticky device error. */
+qsgw_status qsgw_sigc_finalize(qsgw_ctx *ctx, void *I);
+
 /* ---- diagnostics (no counterpart in the paper) ---------------------------------------------
  * Exercises the bounded device-side wait that every pipeline barrier of the tensor-core kernel
  * uses: one thread waits on an mbarrier phase that nothing completes and gives up after

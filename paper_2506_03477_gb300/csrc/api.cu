@@ -59,6 +59,20 @@ struct qsgw_ctx {
   std::vector<int> fill;       // columns staged per bin
   void** d_dptr = nullptr;     // [n_bins] gather destinations of one call
   std::vector<void*> h_dptr;
+  // imaginary-axis correlation self-energy (qsgw_sigc_init): q[0] accumulates the product
+  // D Z^T of the stacked operand [conj(D); Z] (rows 0..n_qp and Y3..Y3+n_qp), q[1] the product
+  // D of [w conj(Z); W^c] for one batch of bands (rows 0..M and Y0..Y0+n_pb)
+  bool sigc = false;
+  SigcMesh smesh{};
+  int sc_nqp = 0, sc_npb = 0, sc_nbb = 0, sc_Y3 = 0;
+  void* d_wsc = nullptr;  // integration weights of one call
+  size_t wsc_cap = 0;
+  void* d_zt = nullptr;  // a batch of Z, transposed
+  size_t zt_cap = 0;
+  void* d_z2 = nullptr;  // stacked operand of D
+  size_t z2_cap = 0;
+  void* d_z3 = nullptr;  // stacked operand of I
+  size_t z3_cap = 0;
   cudaStream_t stream = nullptr;
   std::vector<QAcc> q;
   int* d_err = nullptr;
@@ -392,20 +406,48 @@ qsgw_status spectral_flush(qsgw_ctx* c, const std::vector<int>& js) {
   for (int j : js) c->fill[j] = 0;
   return QSGW_OK;
 }
+
+// ---- imaginary-axis correlation self-energy
+constexpr int kSigcRows = 4096;  // rows (band, target) of one batch of the product D
+constexpr int kSigcAlign = 128;  // row offset of the second row set: a multiple of every tile width
+
+// The product of two row sets of a stacked operand Z (column-major, S rows, K columns): rows I <
+// rows_i against rows J >= col0, with weight 1, into accumulator q.
+qsgw_status sigc_product(qsgw_ctx* c, int q, const void* Z, int S, long long K, int rows_i, int col0) {
+  QAcc& a = c->q[q];
+  if (c->prec == QSGW_FP64) {
+    qsgw_status st = grow(reinterpret_cast<void**>(&c->d_w), &c->w_cap, sizeof(double) * (size_t)K);
+    if (st != QSGW_OK) return st;
+    launch_weights_given_fp64(c->d_one, 1, K, c->d_w, c->d_err, c->stream);
+    const int ti_end = (rows_i + 63) / 64, tj0 = col0 / 64;
+    const int Sl = herk_fp64_slices(a.n_pad, 1, K, ti_end, tj0);
+    if (Sl > 1) {
+      st = grow(&c->d_part, &c->part_cap, sizeof(double2) * (size_t)Sl * a.n_pad * a.n_pad);
+      if (st != QSGW_OK) return st;
+    }
+    launch_herk_fp64(static_cast<const double2*>(Z), S, S, a.n_pad, K, c->d_w, K, 1, Sl, static_cast<double2*>(a.acc),
+                     static_cast<double2*>(c->d_part), c->stream, ti_end, tj0);
+    return cuda_status(cudaGetLastError());
+  }
+  MixedBlock b{Z, S, S, a.n_pad, (int)K, 1, nullptr, nullptr, static_cast<float4*>(a.acc), true, c->d_one};
+  b.rows_i = rows_i;
+  b.col0 = col0;
+  return mixed_accumulate_batch(c->mixed, 1, &b, c->g, c->d_err, c->stream);
+}
 }  // namespace
 
 extern "C" {
 
 qsgw_status qsgw_chi0_accumulate(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
                                  const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
-  if (c && (c->sigx || c->spectral)) return QSGW_ERR_STATE;
+  if (c && (c->sigx || c->spectral || c->sigc)) return QSGW_ERR_STATE;
   return accumulate_any(c, q, Z, false, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
 }
 
 qsgw_status qsgw_chi0_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long long ldz, int n_occ, int n_unocc,
                                      const double* eps_occ, const double* eps_unocc, int n_omega,
                                      const double* omega) {
-  if (c && (c->sigx || c->spectral)) return QSGW_ERR_STATE;
+  if (c && (c->sigx || c->spectral || c->sigc)) return QSGW_ERR_STATE;
   return accumulate_any(c, q, Z, true, ldz, n_occ, n_unocc, eps_occ, eps_unocc, n_omega, omega);
 }
 
@@ -430,7 +472,7 @@ qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long lon
 
 qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
   if (!c || n_blocks < 1 || n_blocks > 32 || !blocks) return QSGW_ERR_ARG;
-  if (c->sigx || c->spectral) return QSGW_ERR_STATE;
+  if (c->sigx || c->spectral || c->sigc) return QSGW_ERR_STATE;
   MixedBlock mb[32];
   for (int i = 0; i < n_blocks; ++i) {
     const qsgw_block& b = blocks[i];
@@ -460,6 +502,7 @@ qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_blo
 
 qsgw_status qsgw_chi0_finalize(qsgw_ctx* c, int q, void* chi0) {
   if (!c || q < 0 || q >= c->n_q || !chi0) return QSGW_ERR_ARG;
+  if (c->spectral || c->sigc) return QSGW_ERR_STATE;  // their own finalize calls read them out
   const QAcc& a = c->q[q];
   launch_finalize_chi(a.acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, a.n_pb, a.n_pad, c->g.L, c->spin,
                       static_cast<double2*>(chi0), c->stream);
@@ -470,7 +513,7 @@ qsgw_status qsgw_chi0_finalize(qsgw_ctx* c, int q, void* chi0) {
 qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps_out, int correlation_only,
                          int* info) {
   if (!c || q < 0 || q >= c->n_q || !v || !W || !info) return QSGW_ERR_ARG;
-  if (c->sigx || c->spectral) return QSGW_ERR_STATE;
+  if (c->sigx || c->spectral || c->sigc) return QSGW_ERR_STATE;
   const QAcc& a = c->q[q];
   const int n = a.n_pb, L = c->g.L;
   const size_t nn = (size_t)n * n;
@@ -551,7 +594,7 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   if (c->d_part) cudaFree(c->d_part);
   if (c->d_zstage) cudaFree(c->d_zstage);
   for (void* p : {(void*)c->d_edges, (void*)c->d_one, (void*)c->d_offsets, (void*)c->d_counts, c->d_bins, c->d_perm,
-                  c->d_zsort, c->d_stage, (void*)c->d_dptr})
+                  c->d_zsort, c->d_stage, (void*)c->d_dptr, c->d_wsc, c->d_zt, c->d_z2, c->d_z3})
     if (p) cudaFree(p);
   if (c->cstream) cudaStreamSynchronize(c->cstream);
   for (int i = 0; i < 2; ++i) {
@@ -733,6 +776,88 @@ qsgw_status qsgw_spectral_real_axis(qsgw_ctx* c, const void* S, int n_out, const
   return st;
 }
 
+// ---- imaginary-axis correlation self-energy: Eq. (sigci) -----------------------------------------
+qsgw_status qsgw_sigc_init(qsgw_ctx** ctx, int n_qp, int n_pb, int n_omega, const double* omega, qsgw_prec prec,
+                           void* cuda_stream) {
+  if (!ctx) return QSGW_ERR_ARG;
+  *ctx = nullptr;
+  if (n_qp < 1 || n_qp > kSigcRows || n_pb < 1 || n_pb > 8192 || n_omega < 1 || n_omega > kMaxOmega || !omega)
+    return QSGW_ERR_ARG;
+  for (int i = 0; i < n_omega; ++i)
+    if (!std::isfinite(omega[i]) || !(omega[i] > 0.0) || (i > 0 && !(omega[i] > omega[i - 1]))) return QSGW_ERR_ARG;
+  if (prec == QSGW_MIXED_BF16X3 && mixed_tile_cols(1) != kSigcAlign) return QSGW_ERR_ARG;
+  const int nbb = std::max(1, kSigcRows / n_qp);
+  const int Y3 = pad_to(n_qp, kSigcAlign);
+  const int npb[2] = {Y3 + n_qp, pad_to(nbb * n_qp, kSigcAlign) + n_pb};
+  const double omega0 = 0.0;
+  qsgw_status st = qsgw_chi0_init(ctx, 2, npb, 1, &omega0, 1.0, prec, cuda_stream);
+  if (st != QSGW_OK) return st;
+  qsgw_ctx* c = *ctx;
+  c->sigc = true;
+  c->sc_nqp = n_qp;
+  c->sc_npb = n_pb;
+  c->sc_nbb = nbb;
+  c->sc_Y3 = Y3;
+  c->smesh.L = n_omega;
+  for (int i = 0; i < n_omega; ++i) c->smesh.om[i] = omega[i];
+  const double one = 1.0;
+  cudaError_t e = cudaMalloc(&c->d_one, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_one, &one, sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    qsgw_chi0_destroy(c);
+    *ctx = nullptr;
+    return cuda_status(e);
+  }
+  return QSGW_OK;
+}
+
+qsgw_status qsgw_sigc_accumulate(qsgw_ctx* c, const void* Z, long long ldz, int n_band, const double* e_qp,
+                                 const double* e_band, const void* Wc) {
+  if (!c || !Z || !e_qp || !e_band || !Wc || n_band < 1) return QSGW_ERR_ARG;
+  if (!c->sigc) return QSGW_ERR_STATE;
+  const int n_qp = c->sc_nqp, n_pb = c->sc_npb, L = c->smesh.L, Y3 = c->sc_Y3;
+  if (ldz < n_pb || (long long)n_band * n_qp > (1LL << 30)) return QSGW_ERR_ARG;
+  if (!is_device_ptr(Z) || !is_device_ptr(e_qp) || !is_device_ptr(e_band) || !is_device_ptr(Wc)) return QSGW_ERR_ARG;
+  const bool z32 = c->prec != QSGW_FP64;
+  const size_t elt = z32 ? sizeof(float2) : sizeof(double2);
+  const long long NT = (long long)n_band * n_qp;
+  const int nbb = std::min(c->sc_nbb, n_band);
+  const int Mmax = nbb * n_qp, S2max = pad_to(Mmax, kSigcAlign) + n_pb, S3 = Y3 + n_qp;
+  qsgw_status st = grow(&c->d_wsc, &c->wsc_cap, sizeof(double) * (size_t)NT * L);
+  if (st == QSGW_OK) st = grow(&c->d_zt, &c->zt_cap, sizeof(double2) * (size_t)Mmax * n_pb);
+  if (st == QSGW_OK) st = grow(&c->d_z2, &c->z2_cap, elt * (size_t)S2max * L * n_pb);
+  if (st == QSGW_OK) st = grow(&c->d_z3, &c->z3_cap, elt * (size_t)S3 * nbb * n_pb);
+  if (st != QSGW_OK) return st;
+  double* w = static_cast<double*>(c->d_wsc);
+  launch_sigc_weights(e_qp, e_band, n_qp, n_band, c->smesh, w, c->d_err, c->stream);
+  const AccKind kind = z32 ? ACC_DF32 : ACC_FP64;
+  for (int b0 = 0; b0 < n_band; b0 += nbb) {
+    const int nb = std::min(nbb, n_band - b0), M = nb * n_qp, Y0 = pad_to(M, kSigcAlign), S2 = Y0 + n_pb;
+    double2* Zt = static_cast<double2*>(c->d_zt);
+    launch_transpose_cols(static_cast<const double2*>(Z), ldz, n_pb, (long long)b0 * n_qp, M, Zt, c->stream);
+    launch_sigc_stack_d(Zt, M, n_pb, w, NT, (long long)b0 * n_qp, L, static_cast<const double2*>(Wc), Y0, c->d_z2,
+                        z32, c->stream);
+    QSGW_CK(cudaMemsetAsync(c->q[1].acc, 0, c->q[1].bytes, c->stream));
+    st = sigc_product(c, 1, c->d_z2, S2, (long long)L * n_pb, M, Y0);
+    if (st != QSGW_OK) return st;
+    launch_sigc_stack_i(c->q[1].acc, kind, c->q[1].n_pad, Y0, Zt, n_qp, nb, n_pb, Y3, c->d_z3, z32, c->stream);
+    st = sigc_product(c, 0, c->d_z3, S3, (long long)nb * n_pb, n_qp, Y3);
+    if (st != QSGW_OK) return st;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+qsgw_status qsgw_sigc_finalize(qsgw_ctx* c, void* I) {
+  if (!c || !I) return QSGW_ERR_ARG;
+  if (!c->sigc) return QSGW_ERR_STATE;
+  if (!is_device_ptr(I)) return QSGW_ERR_ARG;
+  launch_sigc_readout(c->q[0].acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, c->q[0].n_pad, c->sc_nqp, c->sc_Y3,
+                      static_cast<double2*>(I), c->stream);
+  QSGW_CK(cudaGetLastError());
+  return take_device_error(c);
+}
+
 qsgw_status qsgw_chi0_block_noalloc(const void* Z, long long ldz, int n_pb, int n_occ, int n_unocc,
                                     const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega,
                                     double spin_factor, void* chi0, void* cuda_stream) {
@@ -767,7 +892,7 @@ qsgw_status qsgw_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, in
 qsgw_status qsgw_chi0_accumulate_synthetic(qsgw_ctx* c, int q, unsigned long long seed, int gen_q, int k_begin,
                                            int k_end, int n_occ, const int* n_unocc_per_k, const double* eps_occ,
                                            const double* eps_unocc, double s_div) {
-  if (c && (c->sigx || c->spectral)) return QSGW_ERR_STATE;
+  if (c && (c->sigx || c->spectral || c->sigc)) return QSGW_ERR_STATE;
   if (!c || q < 0 || q >= c->n_q || k_begin < 0 || k_end <= k_begin || n_occ < 1 || !n_unocc_per_k || !eps_occ ||
       !eps_unocc || !(s_div > 0.0) || gen_q < 0 || gen_q > 0xFFFFFF)
     return QSGW_ERR_ARG;

@@ -32,9 +32,12 @@ void launch_weights_given_fp64(const double* v, int period, long long K, double*
 // acc[l][J][I] += sum_r w[l][r] conj(Z[I,r]) Z[J,r] on upper-triangle 64x64 tiles. With S > 1 the
 // columns are cut into S slices that sum into part ([S][L][n_pad][n_pad], caller's scratch) and are
 // then added to acc in slice order; herk_fp64_slices picks S (1 unless output tiles are scarce).
-int herk_fp64_slices(int n_pad, int L, long long K);
+// ti_end > 0 restricts the output to the block of I tiles [0, ti_end) and J tiles [tj0, n_pad/64)
+// (tj0 >= ti_end): an off-diagonal block, i.e. a general product of two row sets of Z.
+int herk_fp64_slices(int n_pad, int L, long long K, int ti_end = 0, int tj0 = 0);
 void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
-                      long long ldw, int L, int S, double2* acc, double2* part, cudaStream_t s);
+                      long long ldw, int L, int S, double2* acc, double2* part, cudaStream_t s, int ti_end = 0,
+                      int tj0 = 0);
 
 // ---- shared epilogues (kernels_epsw.cu)
 // Accumulator formats: FP64 complex (double2 [l][J][I]) or double-float planes (float2 hi/lo [l][re|im][J][I]).
@@ -61,6 +64,29 @@ void launch_gather_bins(const double2* Z, long long ldz, int n_pb, const int* pe
 // S [nb][n][n] exactly Hermitian, out [n_out][n][n], column-major complex128).
 void launch_hilbert(const double2* S, int n, int nb, int n_out, const double* K, const int* bins_out,
                     const double* coef, double2* out, cudaStream_t s);
+
+// ---- imaginary-axis correlation self-energy, Eq. (sigci) (sigc.cu)
+struct SigcMesh {
+  double om[kMaxOmega];  // the imaginary frequencies of W^c, increasing, om[0] > 0
+  int L;
+};
+// w[i * NT + n' * n_qp + n] = w_i(e_qp[n] - e_band[n']) for every band n' < n_band and target n,
+// NT = n_band * n_qp; non-finite energies set DEV_DOMAIN and weight 0.
+void launch_sigc_weights(const double* e_qp, const double* e_band, int n_qp, int n_band, const SigcMesh& m,
+                         double* w, int* d_err, cudaStream_t s);
+// Zt (column-major M x n_pb) = transpose of columns [c0, c0 + M) of Z (column-major n_pb x ..., ldz).
+void launch_transpose_cols(const double2* Z, long long ldz, int n_pb, long long c0, int M, double2* Zt, cudaStream_t s);
+// Stacked operand of the product D = sum_i w_i conj(Z) W^c_i (column (i, mu), S2 = Y0 + n_pb rows):
+// rows [0, M) w[i * NT + row0 + row] Zt[row, mu]; rows [M, Y0) zero; rows Y0 + nu conj(Wc_i[nu, mu]).
+void launch_sigc_stack_d(const double2* Zt, int M, int n_pb, const double* w, long long NT, long long row0, int L,
+                         const double2* Wc, int Y0, void* Z2, bool z32, cudaStream_t s);
+// Stacked operand of I -= D Z^T over the columns (band b, nu) of nb bands (S3 = Y3 + n_qp rows):
+// rows [0, n_qp) conj(D(b n_qp + n, nu)) read from the step-2 accumulator (element (I, J = Y0 + nu));
+// rows [n_qp, Y3) zero; rows Y3 + m Zt[b n_qp + m, nu].
+void launch_sigc_stack_i(const void* accD, AccKind kind, int n_padD, int Y0, const double2* Zt, int n_qp, int nb,
+                         int n_pb, int Y3, void* Z3, bool z32, cudaStream_t s);
+// out[m * n_qp + n] = -(accumulator element (I = n, J = Y3 + m)).
+void launch_sigc_readout(const void* accI, AccKind kind, int n_padI, int n_qp, int Y3, double2* out, cudaStream_t s);
 
 // ---- synthetic Z (synth.cu)
 void launch_synth_z(unsigned long long seed, int gen_q, int k, int n_pb, int n_occ, int n_unocc, double s_div,

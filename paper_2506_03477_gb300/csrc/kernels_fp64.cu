@@ -55,15 +55,16 @@ void launch_weights_given_fp64(const double* v, int period, long long K, double*
 constexpr int kT = 64;   // output tile (I and J)
 constexpr int kKS = 16;  // K-step (columns staged per iteration)
 
-// grid: x = J tile, y = I tile, z = frequency + L * K-slice. Tiles strictly below the diagonal exit
-// at once. With S = 1 the tile is added to acc; with S > 1 (few output tiles) slice sk covers
+// grid: x = J tile - tj0, y = I tile, z = frequency + L * K-slice. Tiles strictly below the diagonal
+// exit at once. With tj0 > 0 and fewer I tiles than J tiles the grid covers one off-diagonal block
+// of the output: rows of I tiles [0, gridDim.y), columns of J tiles [tj0, n_pad / 64). With S = 1 the tile is added to acc; with S > 1 (few output tiles) slice sk covers
 // columns [K sk / S, K (sk + 1) / S) and stores its tile into its own partial buffer part[sk], which
 // herk_fp64_reduce_kernel then adds to acc in slice order (deterministic).
 __global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
                                                         int n_pad, long long K, const double* __restrict__ w,
-                                                        long long ldw, int L, int S, double2* __restrict__ acc,
-                                                        double2* __restrict__ part) {
-  const int tj = blockIdx.x, ti = blockIdx.y, l = blockIdx.z % L, sk = blockIdx.z / L;
+                                                        long long ldw, int L, int S, int tj0,
+                                                        double2* __restrict__ acc, double2* __restrict__ part) {
+  const int tj = blockIdx.x + tj0, ti = blockIdx.y, l = blockIdx.z % L, sk = blockIdx.z / L;
   if (tj < ti) return;
   const long long r_begin = K * sk / S, r_end = K * (sk + 1) / S;
   __shared__ double2 sA[kKS][kT];
@@ -135,9 +136,10 @@ __global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restric
 
 // acc += sum over slices sk = 0 .. S-1 of part[sk], on the upper-triangle tiles; grid as the HERK
 // without the slice dimension.
-__global__ void __launch_bounds__(256) herk_fp64_reduce_kernel(int n_pad, int L, int S, const double2* __restrict__ part,
+__global__ void __launch_bounds__(256) herk_fp64_reduce_kernel(int n_pad, int L, int S, int tj0,
+                                                               const double2* __restrict__ part,
                                                                double2* __restrict__ acc) {
-  const int tj = blockIdx.x, ti = blockIdx.y, l = blockIdx.z;
+  const int tj = blockIdx.x + tj0, ti = blockIdx.y, l = blockIdx.z;
   if (tj < ti) return;
   const size_t nn = (size_t)n_pad * n_pad;
   for (int e = threadIdx.x; e < kT * kT; e += 256) {
@@ -152,8 +154,10 @@ __global__ void __launch_bounds__(256) herk_fp64_reduce_kernel(int n_pad, int L,
   }
 }
 
-int herk_fp64_slices(int n_pad, int L, long long K) {
-  const long long tiles = (long long)(n_pad / kT) * (n_pad / kT + 1) / 2 * L;
+int herk_fp64_slices(int n_pad, int L, long long K, int ti_end, int tj0) {
+  const int nt = n_pad / kT;
+  const long long tiles =
+      (ti_end > 0 ? (long long)ti_end * (nt - tj0) : (long long)nt * (nt + 1) / 2) * L;
   const long long want = 2 * 152;  // two CTAs per SM of a GB300
   long long S = tiles >= want ? 1 : (want + tiles - 1) / tiles;
   const long long steps = (K + kKS - 1) / kKS;
@@ -163,10 +167,11 @@ int herk_fp64_slices(int n_pad, int L, long long K) {
 }
 
 void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
-                      long long ldw, int L, int S, double2* acc, double2* part, cudaStream_t s) {
-  dim3 grid(n_pad / kT, n_pad / kT, L * S);
-  herk_fp64_kernel<<<grid, 256, 0, s>>>(Z, ldz, n_pb, n_pad, K, w, ldw, L, S, acc, part);
-  if (S > 1) herk_fp64_reduce_kernel<<<dim3(n_pad / kT, n_pad / kT, L), 256, 0, s>>>(n_pad, L, S, part, acc);
+                      long long ldw, int L, int S, double2* acc, double2* part, cudaStream_t s, int ti_end, int tj0) {
+  const int nt = n_pad / kT, ny = ti_end > 0 ? ti_end : nt;
+  dim3 grid(nt - tj0, ny, L * S);
+  herk_fp64_kernel<<<grid, 256, 0, s>>>(Z, ldz, n_pb, n_pad, K, w, ldw, L, S, tj0, acc, part);
+  if (S > 1) herk_fp64_reduce_kernel<<<dim3(nt - tj0, ny, L), 256, 0, s>>>(n_pad, L, S, tj0, part, acc);
 }
 
 }  // namespace qsgw

@@ -222,6 +222,7 @@ struct PrepRowsBlk {
   float* zmax;
   int* expA;
   int n_pb, n_pad, n_kb, n_jt, n_ch, n_it;
+  int a_rows, b_row0;  // rows I < a_rows need row digit planes, rows I >= b_row0 the column copy
 };
 struct PrepRowsArgs {
   PrepRowsBlk b[kMaxBlocks];
@@ -262,7 +263,9 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
   }
   const float sA = exp2i(eA);
   const int jt = I / TJ, jj = I % TJ;
-  const bool braw_ok = jt < n_jt;
+  const bool braw_ok = jt < n_jt && I >= B.b_row0;
+  const bool need_a = it * TI < B.a_rows;  // CTA-uniform: b_row0 is a multiple of the tile rows
+  if (!need_a && !(it * TI + TI > B.b_row0)) return;
   for (int kbl = 0; kbl < KB_PER_CH; ++kbl) {
     const int kb = c * KB_PER_CH + kbl;
     float a[4], b[4];
@@ -275,6 +278,7 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
       b[rr] = (float)z.y;
       if (braw_ok) braw[(((size_t)jt * n_kb + kb) * KBR + q * 4 + rr) * TJ + jj] = make_float2(a[rr], b[rr]);
     }
+    if (!need_a) continue;
     float da[3][4], db[3][4];
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
@@ -839,6 +843,8 @@ static int tile_width(int L) {
   return 0;
 }
 
+int mixed_tile_cols(int L) { return L >= 1 && L <= kMaxOmega ? tile_width(L) : 0; }
+
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static bool herk_set_attributes() {
@@ -847,25 +853,32 @@ static bool herk_set_attributes() {
 }
 
 // Device list of the tiles on or above the diagonal for one (n_pb, TJ), cached in the scratch.
-static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, const int2** out, int* count) {
+static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, int rows_i, int col0, const int2** out,
+                             int* count) {
   for (auto& e : s.tile_lists)
-    if (e.n_pb == n_pb && e.tj == TJ) {
+    if (e.n_pb == n_pb && e.tj == TJ && e.rows_i == rows_i && e.col0 == col0) {
       *out = e.tiles;
       *count = e.count;
       return QSGW_OK;
     }
   std::vector<int2> tl;
   const int n_it = n_pad / TI, n_jt = (n_pb + TJ - 1) / TJ;
-  for (int it = 0; it < n_it; ++it)
-    for (int jt = 0; jt < n_jt; ++jt)
-      if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) tl.push_back(make_int2(it, jt));
+  if (rows_i > 0) {  // the off-diagonal block: I tiles covering rows [0, rows_i), J tiles from col0
+    for (int it = 0; it * TI < rows_i; ++it)
+      for (int jt = col0 / TJ; jt < n_jt; ++jt) tl.push_back(make_int2(it, jt));
+  } else {
+    for (int it = 0; it < n_it; ++it)
+      for (int jt = 0; jt < n_jt; ++jt)
+        if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) tl.push_back(make_int2(it, jt));
+  }
+  if (tl.empty()) return QSGW_ERR_ARG;
   int2* d = nullptr;
   if (cudaMalloc(&d, tl.size() * sizeof(int2)) != cudaSuccess) return QSGW_ERR_NOMEM;
   if (cudaMemcpy(d, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(d);
     return QSGW_ERR_CUDA;
   }
-  s.tile_lists.push_back({n_pb, TJ, (int)tl.size(), d});
+  s.tile_lists.push_back({n_pb, TJ, rows_i, col0, (int)tl.size(), d});
   *out = d;
   *count = (int)tl.size();
   return QSGW_OK;
@@ -946,7 +959,8 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     const Plan& P = pl[b];
     const MixedBlock& B = in[b];
     BlockDesc& d = a.blk[b];
-    qsgw_status st = tile_list(s, B.n_pb, B.n_pad, TJ, &d.tiles, &d.n_tiles);
+    if (B.rows_i > 0 && (B.col0 % TJ != 0 || B.col0 < B.rows_i || B.col0 >= B.n_pb)) return QSGW_ERR_ARG;
+    qsgw_status st = tile_list(s, B.n_pb, B.n_pad, TJ, B.rows_i, B.col0, &d.tiles, &d.n_tiles);
     if (st != QSGW_OK) return st;
     d.aplanes = base + P.o_a;
     d.braw = reinterpret_cast<float2*>(base + P.o_raw);
@@ -968,7 +982,8 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     const int t = B.z32 ? 1 : 0;
     pr[t].b[nr[t]++] = PrepRowsBlk{B.Z, B.ldz, P.K, base + P.o_a, reinterpret_cast<float2*>(base + P.o_raw),
                                    reinterpret_cast<float*>(base + P.o_zmax), reinterpret_cast<int*>(base + P.o_exp),
-                                   B.n_pb, B.n_pad, P.n_kb, P.n_jt, P.n_ch, P.n_it};
+                                   B.n_pb, B.n_pad, P.n_kb, P.n_jt, P.n_ch, P.n_it,
+                                   B.rows_i > 0 ? B.rows_i : B.n_pad, B.rows_i > 0 ? B.col0 : 0};
     max_ch = std::max(max_ch, P.n_ch);
     max_chr[t] = std::max(max_chr[t], P.n_ch);
     max_it[t] = std::max(max_it[t], P.n_it);
@@ -1115,7 +1130,7 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   pr.TJ = TJ;
   pr.b[0] = PrepRowsBlk{Z, ldz, K, base + o_a, reinterpret_cast<float2*>(base + o_raw),
                         reinterpret_cast<float*>(base + o_zmax), reinterpret_cast<int*>(base + o_exp),
-                        n_pb, n_pad, n_kb, n_jt, n_ch, n_it};
+                        n_pb, n_pad, n_kb, n_jt, n_ch, n_it, n_pad, 0};
   prep_rows_kernel<double2><<<dim3(n_ch, n_it, 1), 256, 0, stream>>>(pr);
   a.fscr = reinterpret_cast<float2*>(base + o_fscr);
   a.pbuf = reinterpret_cast<float2*>(base + o_fscr + (size_t)cap_ctas * fscr_cta);

@@ -10,7 +10,7 @@ namespace qsgw {
 // accumulate call: digit planes of the row operand, FP32 copy of Z for the column operand,
 // FP32 weights, per-chunk maxima / exponents, and cached device lists of upper-triangle tiles.
 struct TileList {
-  int n_pb, tj, count;
+  int n_pb, tj, rows_i, col0, count;
   int2* tiles;
 };
 struct MixedScratch {
@@ -35,7 +35,13 @@ struct MixedBlock {
   bool z32;  // Z holds complex64: the mixed path rounds every element to FP32 first anyway
   // Given weights (L = 1) instead of the weights from Delta: w_r = wv[r mod n_unocc], wv > 0.
   const double* wv;
+  // rows_i > 0: only the off-diagonal block of rows I < rows_i and columns J >= col0 (a multiple
+  // of mixed_tile_cols(L), >= rows_i) is computed: the product of two row sets of Z.
+  int rows_i = 0, col0 = 0;
 };
+
+// Columns per output tile of the tensor-core kernel for L frequencies (rows per tile: 64).
+int mixed_tile_cols(int L);
 
 // Prep of every block, then one persistent tensor-core launch over all (block, tile, chunk)
 // items. Blocks must belong to distinct q-points (distinct accumulators); at most 32 blocks.

@@ -32,6 +32,7 @@ EXPORTS = [
     "qsgw_chi0_accumulate_batch", "qsgw_chi0_block_noalloc", "qsgw_chi0_accumulate_c64",
     "qsgw_sigx_init", "qsgw_sigx_accumulate", "qsgw_sigx_accumulate_c64", "qsgw_selftest_wait_timeout",
     "qsgw_spectral_init", "qsgw_spectral_accumulate", "qsgw_spectral_finalize", "qsgw_spectral_real_axis",
+    "qsgw_sigc_init", "qsgw_sigc_accumulate", "qsgw_sigc_finalize",
 ]
 
 
@@ -72,6 +73,9 @@ def load():
         "qsgw_spectral_accumulate": [_p, _p, _ll, _i, _i, _p, _p],
         "qsgw_spectral_finalize": [_p, _p],
         "qsgw_spectral_real_axis": [_p, _p, _i, P(_i), _p],
+        "qsgw_sigc_init": [P(_p), _i, _i, _i, P(_d), _i, _p],
+        "qsgw_sigc_accumulate": [_p, _p, _ll, _i, _p, _p, _p],
+        "qsgw_sigc_finalize": [_p, _p],
         "qsgw_chi0_finalize": [_p, _i, _p],
         "qsgw_eps_inv": [_p, _i, _p, _p, _p, _i, P(_i)],
         "qsgw_chi0_reset": [_p, _i],
@@ -188,6 +192,25 @@ def qsgw_spectral_real_axis(ctx: int, S, bins_out, out):
     b = list(bins_out)
     arr = (_i * len(b))(*b)
     _check(load().qsgw_spectral_real_axis(ctx, _addr(S), len(b), arr, _addr(out)), "qsgw_spectral_real_axis")
+
+
+def qsgw_sigc_init(n_qp: int, n_pb: int, omega, prec: int = QSGW_FP64, stream=None) -> int:
+    """Context for the imaginary-axis correlation self-energy, Eq. (sigci) (see include/qsgw.h)."""
+    om = [float(x) for x in omega]
+    arr = (_d * len(om))(*om)
+    ctx = _p()
+    _check(load().qsgw_sigc_init(ctypes.byref(ctx), int(n_qp), int(n_pb), len(om), arr, int(prec), _stream(stream)),
+           "qsgw_sigc_init")
+    return ctx.value
+
+
+def qsgw_sigc_accumulate(ctx: int, Z, ldz: int, n_band: int, e_qp, e_band, Wc):
+    _check(load().qsgw_sigc_accumulate(ctx, _addr(Z), int(ldz), int(n_band), _addr(e_qp), _addr(e_band), _addr(Wc)),
+           "qsgw_sigc_accumulate")
+
+
+def qsgw_sigc_finalize(ctx: int, I):
+    _check(load().qsgw_sigc_finalize(ctx, _addr(I)), "qsgw_sigc_finalize")
 
 
 def qsgw_selftest_wait_timeout(limit_seconds: float, stream=None) -> int:
