@@ -148,3 +148,43 @@ def test_sigc_errors(N):
         assert ei.value.status == -7
     finally:
         N.qsgw_chi0_destroy(ctx)
+
+
+def test_sigc_medium_shapes_sampled(N):
+    """I^c at the benchmark's shapes: n_pb = 1500, 12 frequencies, n_qp = 64 targets, 64 bands (one
+    band batch of 4096 rows), mixed precision, W^c of plasmon-pole form -A/(1 + w^2/Wp^2) P with P
+    Hermitian positive definite. Checked on 4 sampled targets (rows and columns) against the
+    oracle, which needs only those targets' columns of Z."""
+    from synthetic import MEDIUM as W
+    n_qp, n_pb, n_band = 64, 1500, 64
+    om = W.omega
+    rng = np.random.default_rng(43)
+    B = rng.standard_normal((n_pb, n_pb)) + 1j * rng.standard_normal((n_pb, n_pb))
+    P = B @ B.conj().T / n_pb
+    P = 0.5 * (P + P.conj().T)
+    f = 0.8 / (1.0 + (om / 0.6) ** 2)
+    Wc = -f[:, None, None] * P[None]
+    Zc = z_block(47, 2, 0, n_pb, n_band, n_qp, 200.0)
+    e_qp = np.sort(rng.uniform(-0.3, 0.4, n_qp))
+    e_band = np.sort(rng.uniform(-0.8, 3.0, n_band))
+    ctx = N.qsgw_sigc_init(n_qp, n_pb, om, N.QSGW_MIXED_BF16X3)
+    try:
+        Zd, eq, eb = _dev(Zc), _dev(e_qp), _dev(e_band)
+        Wd = _dev(np.ascontiguousarray(Wc.transpose(0, 2, 1)))
+        N.qsgw_sigc_accumulate(ctx, Zd, n_pb, n_band, eq, eb, Wd)
+        out = torch.empty((n_qp, n_qp), dtype=torch.complex128, device="cuda")
+        N.qsgw_sigc_finalize(ctx, out)
+        got = out.cpu().numpy().T
+    finally:
+        N.qsgw_chi0_destroy(ctx)
+    t = np.array([0, 21, 40, 63])
+    cols = (np.arange(n_band)[:, None] * n_qp + t[None, :]).ravel()  # rows (n', t) of the sample
+    Zs = Zc[cols]
+    ref = oracle.sigc([Zs], e_qp[t], [e_band], om, [Wc])
+    A = np.zeros((t.size, t.size))
+    for b in range(n_band):
+        Zb = np.abs(Zs[b * t.size:(b + 1) * t.size])
+        w = np.abs(np.array([oracle.sigc_weights(e - e_band[b], om) for e in e_qp[t]]))
+        A += sum(w[:, i:i + 1] * (Zb @ np.abs(Wc[i]) @ Zb.T) for i in range(om.size))
+    err = np.abs(got[np.ix_(t, t)] - ref)
+    assert np.all(err <= 2e-6 * A), (err / A).max()

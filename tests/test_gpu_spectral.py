@@ -189,3 +189,49 @@ def test_real_axis_output_groups(N, bins_out):
     Pref = oracle.real_axis_chi0(ref, EDGES, bins_out)
     for o in range(len(bins_out)):
         assert rel_fro(P[o], Pref[o]) <= 1e-11, (o, rel_fro(P[o], Pref[o]))
+
+
+def test_realaxis_medium_full_size_sampled(N):
+    """The real-axis route at the benchmark's size and launch configuration: n_pb = 1500, 64 k-points
+    x 40 x 400 columns (Z drawn on the device, one k-point at a time), 156 log bins 0.04 * 1.03^j
+    Ry, mixed precision. S_j of every bin and the real-axis chi0 at four bin centres are checked on
+    a 5 x 5 block of sampled rows against the oracle over all 1,024,000 columns."""
+    from synthetic import MEDIUM as W
+    n, nk, no, nu = 1500, W.n_k, W.n_occ, 400
+    edges = 0.04 * 1.03 ** np.arange(0, 157)
+    nb = edges.size - 1
+    rows = np.array([0, 17, 700, 1250, 1499])
+    bins_out = [30, 80, 120, 150]
+    ctx = N.qsgw_spectral_init(n, edges, N.QSGW_MIXED_BF16X3)
+    try:
+        Z = torch.empty((no * nu, n), dtype=torch.complex128, device="cuda")
+        for k in range(nk):
+            N.qsgw_synth_z(W.seed, 0, k, n, no, nu, W.s_div, Z, n)
+            N.qsgw_spectral_accumulate(ctx, Z, n, no, nu, _dev(eps_occ(W.seed, 0, k, no)), _dev(eps_unocc(W.seed, 0, k, nu)))
+            N.qsgw_chi0_sync(ctx)
+        del Z
+        S = torch.empty((nb, n, n), dtype=torch.complex128, device="cuda")
+        N.qsgw_spectral_finalize(ctx, S)
+        P = torch.empty((len(bins_out), n, n), dtype=torch.complex128, device="cuda")
+        N.qsgw_spectral_real_axis(ctx, S, bins_out, P)
+        r = torch.from_numpy(rows).cuda()
+        Sb = S[:, r][:, :, r].cpu().numpy().transpose(0, 2, 1)
+        Pb = P[:, r][:, :, r].cpu().numpy().transpose(0, 2, 1)
+        del S, P
+    finally:
+        N.qsgw_chi0_destroy(ctx)
+    from synthetic import z_rows
+    ZR = z_rows(W.seed, 0, rows, nk, no, lambda k: nu, W.s_div)
+    d = np.concatenate([oracle.delta(eps_occ(W.seed, 0, k, no), eps_unocc(W.seed, 0, k, nu))[0] for k in range(nk)])
+    ref, outside = oracle.hist_spectral(ZR, ZR, d, edges)
+    assert outside == 0
+    for j in range(nb):
+        if np.linalg.norm(ref[j]) == 0.0:
+            assert np.all(Sb[j] == 0), j
+            continue
+        assert rel_fro(Sb[j], ref[j]) <= 1e-6, (j, rel_fro(Sb[j], ref[j]))
+        dg = np.sqrt(np.abs(np.diag(ref[j])))
+        assert np.all(np.abs(Sb[j] - ref[j]) <= 1e-6 * np.outer(dg, dg) + 1e-300), j
+    Pref = oracle.real_axis_chi0(ref, edges, bins_out)
+    for o in range(len(bins_out)):
+        assert rel_fro(Pb[o], Pref[o]) <= 1e-5, (o, rel_fro(Pb[o], Pref[o]))
