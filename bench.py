@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -71,7 +72,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples in the system's temporary directory; the JSON line carries their summary
+        self.path = os.path.join(tempfile.gettempdir(), f"qsgw_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
