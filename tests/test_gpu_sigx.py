@@ -110,3 +110,31 @@ def test_sigx_and_chi0_contexts_reject_each_other(N):
     finally:
         N.qsgw_chi0_destroy(sx)
         N.qsgw_chi0_destroy(cx)
+
+
+def test_sigx_paper_size_sampled(N):
+    """Sigma^x at the benchmark's (InAs)6(GaSb)6 size: n_qp = 428, 16 k-points x 276 occupied x
+    3139 product-basis functions (13,861,824 columns), Z drawn on the device one k-point at a
+    time, mixed precision. Four sampled rows and columns against the oracle over all columns."""
+    from synthetic import z_rows
+    n_qp, n_pb, n_occ, n_k, seed = 428, 3139, 276, 16, 1
+    rows = np.array([0, 101, 300, 427])
+    ctx = N.qsgw_sigx_init([n_qp], N.QSGW_MIXED_BF16X3)
+    try:
+        Z = torch.empty((n_occ * n_pb, n_qp), dtype=torch.complex128, device="cuda")
+        for k in range(n_k):
+            N.qsgw_synth_z(seed, 7, k, n_qp, n_occ, n_pb, 100.0, Z, n_qp)
+            v = _dev(coulomb_v(seed, k, n_pb))
+            N.qsgw_sigx_accumulate(ctx, 0, Z, n_qp, n_occ, n_pb, v)
+            N.qsgw_chi0_sync(ctx)
+        del Z
+        out = torch.empty((n_qp, n_qp), dtype=torch.complex128, device="cuda")
+        N.qsgw_chi0_finalize(ctx, 0, out)
+        got = out.cpu().numpy().T[np.ix_(rows, rows)]
+    finally:
+        N.qsgw_chi0_destroy(ctx)
+    ZR = z_rows(seed, 7, rows, n_k, n_occ, lambda k: n_pb, 100.0)
+    ref = oracle.sigx(ZR, [n_occ] * n_k, n_pb, np.stack([coulomb_v(seed, k, n_pb) for k in range(n_k)]))
+    assert rel_fro(got, ref) <= 1e-6, rel_fro(got, ref)
+    dg = np.sqrt(np.abs(np.diag(ref)))
+    assert np.all(np.abs(got - ref) <= 1e-6 * np.outer(dg, dg))
