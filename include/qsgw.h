@@ -19,6 +19,14 @@
  *   W_IJ   = sqrt(v_I) [eps^{-1}]_IJ sqrt(v_J)            Eq. (screenedcoulomb)
  *   W^c_IJ = W_IJ - v_I delta_IJ                          Eq. (wc)
  *
+ * The same kernels also give, each in its own section below:
+ *   - the exchange self-energy Sigma^x, Eq. (sigx): a Hermitian update with given column
+ *     weights v_mu(k);
+ *   - the real-axis route, Eqs. (impolf) and (hilbert): the spectral weight of every histogram
+ *     bin of transition energies, then chi0 on the real axis;
+ *   - the imaginary-axis correlation self-energy I^c, Eq. (sigci): D = sum_i w_i conj(Z) W^c_i
+ *     and D Z^T, each as a block of a Hermitian update of a stacked operand.
+ *
  * Conventions shared by every call
  *   - Complex numbers are interleaved (re, im) pairs of double (C99 double complex layout).
  *   - Matrices are column-major: element (I, J) of an n_pb x n_pb matrix is at J*n_pb + I.

@@ -1,5 +1,8 @@
 // C ABI (include/qsgw.h): context, argument validation, host staging, stream ordering, and
 // the eps^{-1} step through cuSOLVER (FP64 Cholesky: potrf + potri, one stream per frequency).
+// Also the host side of Sigma^x (given column weights), of the real-axis route (binning,
+// per-bin staging and flushes, the Hilbert weights) and of I^c (band batches of the two
+// stacked products).
 #include <cusolverDn.h>
 
 #include <algorithm>
