@@ -486,7 +486,7 @@ qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_blo
     for (int j = 0; j < i; ++j)
       if (blocks[j].q == b.q) return QSGW_ERR_ARG;
     if (!is_device_ptr(b.Z) || !is_device_ptr(b.eps_occ) || !is_device_ptr(b.eps_unocc)) return QSGW_ERR_ARG;
-    mb[i] = MixedBlock{b.Z,         b.ldz, a.n_pb, a.n_pad, b.n_occ, b.n_unocc, b.eps_occ,
+    mb[i] = MixedBlock{b.Z, b.ldz, a.n_pb, a.n_pad, b.n_occ, b.n_unocc, b.eps_occ,
                        b.eps_unocc, static_cast<float4*>(a.acc), /*z32*/ false, /*wv*/ nullptr};
   }
   if (c->prec == QSGW_FP64) {
