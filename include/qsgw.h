@@ -142,9 +142,13 @@ qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx *ctx, int n_blocks, const qsgw_b
  * the stream and returns any sticky device error. The accumulator is kept. */
 qsgw_status qsgw_chi0_finalize(qsgw_ctx *ctx, int q, void *chi0);
 
-/* From the current accumulator of q: eps (Eq. dielectricfunction), its FP64 Cholesky
- * factorisation and inverse, and W (Eq. screenedcoulomb), or W^c (Eq. wc) when
- * correlation_only != 0, for every frequency.
+/* From the current accumulator of q: eps (Eq. dielectricfunction), its inverse in FP64, and W
+ * (Eq. screenedcoulomb), or W^c (Eq. wc) when correlation_only != 0, for every frequency. The
+ * inverse is a block sweep over 32 x 32 pivot blocks, each factored by Cholesky: the pivot blocks
+ * are the Schur complements of the leading blocks, so their Cholesky factors are the diagonal
+ * blocks of eps = L L^H, and the cost is that of a Cholesky factorisation plus the inverse from
+ * it. All frequencies go through each launch; the context keeps 3 x 32 x n_pb x n_omega complex
+ * values of scratch for it.
  *   v         device [n_pb], Coulomb eigenvalues v_I > 0 (diagonal MPB basis, Eq. (eqvcoue))
  *   W         device complex128 [n_omega][n_pb][n_pb], full Hermitian
  *   eps_out   NULL or device complex128, same layout: eps before factorisation
@@ -305,10 +309,13 @@ qsgw_status qsgw_selftest_wait_timeout(double limit_seconds, void *cuda_stream);
  *   cuda_stream            stream the work is ordered on; the call synchronises it at the end to
  *                          return device-detected errors (QSGW_ERR_DOMAIN, QSGW_ERR_TIMEOUT)
  * Sizes whose intermediates do not fit the fixed array return QSGW_ERR_ARG (use the context
- * API instead); n_pb <= 256 with n_occ * n_unocc <= 3072 always fits. The first call on a
- * device looks up the array's device address (and raises the kernel's shared-memory limit),
- * so make that first call before any stream capture. All calls share the one array: calls
- * whose GPU work overlaps (other streams, other host threads) race and must not be issued. */
+ * API instead); n_pb <= 256 with n_occ * n_unocc <= 3072 always fits. The space left after the
+ * accumulators and operands holds one flush area per CTA, and the tensor-core grid is capped at
+ * the CTAs it has room for (about 15 at that corner, more for smaller blocks). Every call looks
+ * up the array's device address in the current context (and sets the kernel's shared-memory
+ * limit there), so the call stays valid after the context is reset. All calls share the one
+ * array: calls whose GPU work overlaps (other streams, other host threads) race and must not be
+ * issued. */
 qsgw_status qsgw_chi0_block_noalloc(const void *Z, long long ldz, int n_pb, int n_occ, int n_unocc,
                                     const double *eps_occ, const double *eps_unocc, int n_omega,
                                     const double *omega, double spin_factor, void *chi0, void *cuda_stream);

@@ -1,7 +1,7 @@
 """Build the CUDA library in-tree: paper_2506_03477_gb300/libqsgw.so (sm_103a only).
 
 Each .cu is compiled to an object in parallel (nvcc -gencode arch=compute_103a,code=sm_103a),
-then linked into one shared library against cuSOLVER (FP64 Cholesky of eps)."""
+then linked into one shared library against the CUDA runtime only."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -46,7 +46,7 @@ def build(verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcusolver", "-lcudart"]
+        cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -1,10 +1,8 @@
-// C ABI (include/qsgw.h): context, argument validation, host staging, stream ordering, and
-// the eps^{-1} step through cuSOLVER (FP64 Cholesky: potrf + potri, one stream per frequency).
+// C ABI (include/qsgw.h): context, argument validation, host staging, stream ordering, and the
+// eps -> eps^{-1} -> W sequence (FP64 block sweep with Cholesky pivots, all frequencies per launch).
 // Also the host side of Sigma^x (given column weights), of the real-axis route (binning,
 // per-bin staging and flushes, the Hilbert weights) and of I^c (band batches of the two
 // stacked products).
-#include <cusolverDn.h>
-
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -21,16 +19,6 @@ struct QAcc {
   int n_pad = 0;
   void* acc = nullptr;  // FP64: double2 [L][n_pad][n_pad]; mixed: 2 copies of float2 (hi, lo) [L][re|im][n_pad][n_pad]
   size_t bytes = 0;
-};
-
-// One cuSOLVER handle, stream and workspace per frequency, so the independent Cholesky
-// factorisations of eps(i omega_l) run concurrently (each alone leaves most SMs idle).
-struct SolverLane {
-  cudaStream_t stream = nullptr;
-  cusolverDnHandle_t handle = nullptr;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  cudaEvent_t done = nullptr;
 };
 
 struct qsgw_ctx {
@@ -99,8 +87,13 @@ struct qsgw_ctx {
   cudaEvent_t hfree[2] = {};    // last reader of the slot done (recorded on stream)
   int hslot = 0;
   MixedScratch mixed;
-  SolverLane lanes[kMaxOmega];
-  cudaEvent_t fork = nullptr;
+  // eps^{-1} scratch: the pivot inverses [L][32][32] and the panel buffers P, C [L][32][n_pb]
+  void* d_sbuf = nullptr;
+  size_t sbuf_cap = 0;
+  void* d_pbuf = nullptr;
+  size_t pbuf_cap = 0;
+  void* d_cbuf = nullptr;
+  size_t cbuf_cap = 0;
   int* d_info = nullptr;
 };
 
@@ -521,55 +514,28 @@ qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps
   const int n = a.n_pb, L = c->g.L;
   const size_t nn = (size_t)n * n;
   double2* w = static_cast<double2*>(W);
-  if (!c->d_info) QSGW_CK(cudaMalloc(&c->d_info, sizeof(int) * 2 * kMaxOmega));
-  if (!c->fork) QSGW_CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
-  for (int l = 0; l < L; ++l) {
-    SolverLane& ln = c->lanes[l];
-    if (!ln.stream) {
-      QSGW_CK(cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking));
-      QSGW_CK(cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming));
-      if (cusolverDnCreate(&ln.handle) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
-      if (cusolverDnSetStream(ln.handle, ln.stream) != CUSOLVER_STATUS_SUCCESS) return QSGW_ERR_CUDA;
-    }
-    int lw1 = 0, lw2 = 0;
-    auto* m = reinterpret_cast<cuDoubleComplex*>(w + l * nn);
-    if (cusolverDnZpotrf_bufferSize(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, &lw1) != CUSOLVER_STATUS_SUCCESS ||
-        cusolverDnZpotri_bufferSize(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, &lw2) != CUSOLVER_STATUS_SUCCESS)
-      return QSGW_ERR_CUDA;
-    const size_t lwork = (size_t)(lw1 > lw2 ? lw1 : lw2);
-    qsgw_status st = grow(&ln.ws, &ln.ws_bytes, sizeof(cuDoubleComplex) * (lwork + 1));
-    if (st != QSGW_OK) return st;
-  }
+  if (!c->d_info) QSGW_CK(cudaMalloc(&c->d_info, sizeof(int) * kMaxOmega));
+  qsgw_status st = grow(&c->d_sbuf, &c->sbuf_cap, sizeof(double2) * 32 * 32 * L);
+  if (st == QSGW_OK) st = grow(&c->d_pbuf, &c->pbuf_cap, sizeof(double2) * 32 * (size_t)n * L);
+  if (st == QSGW_OK) st = grow(&c->d_cbuf, &c->cbuf_cap, sizeof(double2) * 32 * (size_t)n * L);
+  if (st != QSGW_OK) return st;
 
   launch_form_eps(a.acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, n, a.n_pad, L, c->spin, v, w, c->stream);
   QSGW_CK(cudaGetLastError());
   if (eps_out) QSGW_CK(cudaMemcpyAsync(eps_out, w, sizeof(double2) * nn * L, cudaMemcpyDeviceToDevice, c->stream));
-  QSGW_CK(cudaEventRecord(c->fork, c->stream));
-  for (int l = 0; l < L; ++l) {
-    SolverLane& ln = c->lanes[l];
-    auto* m = reinterpret_cast<cuDoubleComplex*>(w + l * nn);
-    const int lwork = (int)(ln.ws_bytes / sizeof(cuDoubleComplex) - 1);
-    auto* ws = static_cast<cuDoubleComplex*>(ln.ws);
-    QSGW_CK(cudaStreamWaitEvent(ln.stream, c->fork, 0));
-    if (cusolverDnZpotrf(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, lwork, c->d_info + l) !=
-        CUSOLVER_STATUS_SUCCESS)
-      return QSGW_ERR_CUDA;
-    if (cusolverDnZpotri(ln.handle, CUBLAS_FILL_MODE_LOWER, n, m, n, ws, lwork, c->d_info + kMaxOmega + l) !=
-        CUSOLVER_STATUS_SUCCESS)
-      return QSGW_ERR_CUDA;
-    QSGW_CK(cudaEventRecord(ln.done, ln.stream));
-    QSGW_CK(cudaStreamWaitEvent(c->stream, ln.done, 0));
-  }
-  launch_w_from_inverse(w, n, L, v, correlation_only, c->stream);
+  QSGW_CK(cudaMemsetAsync(c->d_info, 0, sizeof(int) * kMaxOmega, c->stream));
+  launch_eps_inverse(w, n, L, static_cast<double2*>(c->d_sbuf), static_cast<double2*>(c->d_pbuf),
+                     static_cast<double2*>(c->d_cbuf), c->d_info, c->stream);
   QSGW_CK(cudaGetLastError());
-  int hinfo[2 * kMaxOmega];
-  QSGW_CK(cudaMemcpyAsync(hinfo, c->d_info, sizeof(int) * 2 * kMaxOmega, cudaMemcpyDeviceToHost, c->stream));
-  qsgw_status st = take_device_error(c);
+  launch_w_from_inverse(w, n, L, v, correlation_only, -1.0, c->stream);  // the sweep leaves -eps^{-1}
+  QSGW_CK(cudaGetLastError());
+  int hinfo[kMaxOmega];
+  QSGW_CK(cudaMemcpyAsync(hinfo, c->d_info, sizeof(int) * kMaxOmega, cudaMemcpyDeviceToHost, c->stream));
+  st = take_device_error(c);
   if (st != QSGW_OK) return st;
   qsgw_status res = QSGW_OK;
   for (int l = 0; l < L; ++l) {
-    // potrf reports the first non-positive pivot (1-based); potri can only fail after a zero pivot
-    info[l] = hinfo[l] != 0 ? hinfo[l] : hinfo[kMaxOmega + l];
+    info[l] = hinfo[l];  // first non-positive pivot (1-based), as a Cholesky factorisation reports it
     if (info[l] != 0) res = QSGW_ERR_NOT_PD;
   }
   return res;
@@ -609,13 +575,8 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   }
   if (c->cstream) cudaStreamDestroy(c->cstream);
   mixed_free(c->mixed);
-  for (auto& ln : c->lanes) {
-    if (ln.handle) cusolverDnDestroy(ln.handle);
-    if (ln.ws) cudaFree(ln.ws);
-    if (ln.done) cudaEventDestroy(ln.done);
-    if (ln.stream) cudaStreamDestroy(ln.stream);
-  }
-  if (c->fork) cudaEventDestroy(c->fork);
+  for (void* p : {c->d_sbuf, c->d_pbuf, c->d_cbuf})
+    if (p) cudaFree(p);
   if (c->d_info) cudaFree(c->d_info);
   if (c->d_err) cudaFree(c->d_err);
   delete c;

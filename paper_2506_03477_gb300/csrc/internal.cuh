@@ -48,8 +48,16 @@ void launch_finalize_chi(const void* acc, AccKind kind, int n, int n_pad, int L,
 // eps = I - D chi0 D with chi0 = -s * mirror(acc), full matrix.
 void launch_form_eps(const void* acc, AccKind kind, int n, int n_pad, int L, double spin, const double* v,
                      double2* eps, cudaStream_t s);
-// In place: lower triangle of eps^{-1} -> full W = D eps^{-1} D (minus diag(v) if wc).
-void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, cudaStream_t s);
+// In place: lower triangle of sg * eps^{-1} (sg = +-1) -> full W = D eps^{-1} D (minus diag(v) if wc).
+void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, double sg, cudaStream_t s);
+
+// ---- eps^{-1} (epsinv.cu)
+// In place on w ([L][n][n], column-major; the lower triangle of each Hermitian positive definite
+// matrix is read): the lower triangle becomes -eps^{-1}. sbuf: [L][32][32], pbuf and cbuf:
+// [L][32][n] complex128 scratch. d_info[l] (zeroed by the caller) receives the 1-based index of the
+// first non-positive pivot, as a Cholesky factorisation would report it.
+void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, double2* cbuf, int* d_info,
+                        cudaStream_t s);
 
 // ---- real-axis route (spectral.cu)
 // Bin every column by Delta (edges: device [n_bins + 1]), count per bin, exclusive offsets

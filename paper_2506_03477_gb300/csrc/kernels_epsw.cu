@@ -77,10 +77,11 @@ void launch_form_eps(const void* acc, AccKind kind, int n, int n_pad, int L, dou
   launch_readout<1>(acc, kind, n, n_pad, L, spin, v, eps, s);
 }
 
-// In place on w ([L][n][n], column-major): the lower triangle holds eps^{-1}; write the full
-// W = D eps^{-1} D (minus diag(v) when wc != 0). One CTA per lower block pair (bi >= bj): it reads
-// its lower block before writing it and its (never read) mirror block above the diagonal.
-__global__ void w_from_inverse_kernel(double2* __restrict__ w, int n, const double* __restrict__ v, int wc) {
+// In place on w ([L][n][n], column-major): the lower triangle holds sg * eps^{-1} (sg = +-1); write
+// the full W = D eps^{-1} D (minus diag(v) when wc != 0). One CTA per lower block pair (bi >= bj):
+// it reads its lower block before writing it and its (never read) mirror block above the diagonal.
+__global__ void w_from_inverse_kernel(double2* __restrict__ w, int n, const double* __restrict__ v, int wc,
+                                      double sg) {
   const int bj = blockIdx.x, bi = blockIdx.y, l = blockIdx.z;
   if (bi < bj) return;
   __shared__ double2 t[32][33];
@@ -96,7 +97,7 @@ __global__ void w_from_inverse_kernel(double2* __restrict__ w, int n, const doub
     const int ii = tx, jj = y, I = bi * 32 + ii, J = bj * 32 + jj;
     if (I >= n || J >= n) continue;
     double2 x = (bi > bj || ii >= jj) ? t[jj][ii] : make_double2(t[ii][jj].x, -t[ii][jj].y);
-    const double d = sqrt(v[I]) * sqrt(v[J]);
+    const double d = sg * (sqrt(v[I]) * sqrt(v[J]));
     double2 o = make_double2(d * x.x, I == J ? 0.0 : d * x.y);
     if (wc && I == J) o.x -= v[I];
     m[(size_t)J * n + I] = o;
@@ -108,15 +109,15 @@ __global__ void w_from_inverse_kernel(double2* __restrict__ w, int n, const doub
     const int R = bj * 32 + jj, C = bi * 32 + ii;
     if (R >= n || C >= n) continue;
     const double2 x = t[jj][ii];  // X(C, R)
-    const double d = sqrt(v[R]) * sqrt(v[C]);
+    const double d = sg * (sqrt(v[R]) * sqrt(v[C]));
     m[(size_t)C * n + R] = make_double2(d * x.x, -d * x.y);
   }
 }
 
-void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, cudaStream_t s) {
+void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, double sg, cudaStream_t s) {
   const int nb = (n + 31) / 32;
   dim3 grid(nb, nb, L), block(32, 8);
-  w_from_inverse_kernel<<<grid, block, 0, s>>>(w, n, v, wc);
+  w_from_inverse_kernel<<<grid, block, 0, s>>>(w, n, v, wc, sg);
 }
 
 }  // namespace qsgw

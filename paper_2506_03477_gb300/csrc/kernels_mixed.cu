@@ -1026,8 +1026,6 @@ qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long
 // fixed file-scope device array instead of cudaMalloc'd scratch. See qsgw_chi0_block_noalloc.
 constexpr size_t kNoAllocBytes = 64ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-constexpr int kMaxDevices = 64;
-static void* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
 // Upper-triangle tile list of one (n_pb, TJ), in the order tile_list() uses, built on the device.
 __global__ void noalloc_tiles_kernel(int n_pb, int n_it, int n_jt, int TJ, int2* out) {
@@ -1043,13 +1041,13 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   const int L = g.L, TJ = tile_width(L), N = TJ * L;
   if (TJ < 1 || N < 16 || N > 256) return QSGW_ERR_ARG;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QSGW_ERR_CUDA;
-  if (!g_noalloc_ptr[dev]) {  // set-up, once per device, with that device current
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return QSGW_ERR_CUDA;
-    if (!herk_set_attributes()) return QSGW_ERR_CUDA;
-    g_noalloc_ptr[dev] = ptr;
-  }
+  if (cudaGetDevice(&dev) != cudaSuccess) return QSGW_ERR_CUDA;
+  // Set-up on every call, in the current context: the array's device address (a lookup, no
+  // allocation) and the kernel's shared-memory limit. Neither is cached, because both belong to
+  // the context: after cudaDeviceReset the module is loaded again and the array may move.
+  void* scratch = nullptr;
+  if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch) return QSGW_ERR_CUDA;
+  if (!herk_set_attributes()) return QSGW_ERR_CUDA;
   int n_sm = 0;
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QSGW_ERR_CUDA;
   const int n_pad = pad_to(n_pb, kPad);
@@ -1084,7 +1082,7 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   const size_t o_fscr = off, fscr_cta = (size_t)kFscrPerCta * sizeof(float2);
   if (off + 2 * fscr_cta > kNoAllocBytes) return QSGW_ERR_ARG;  // beyond the fixed array: use the context API
   const int cap_ctas = (int)((kNoAllocBytes - off) / (2 * fscr_cta));
-  uint8_t* base = static_cast<uint8_t*>(g_noalloc_ptr[dev]);
+  uint8_t* base = static_cast<uint8_t*>(scratch);
   int* d_err = reinterpret_cast<int*>(base);
   int* counter = d_err + 1;
   // the array keeps the previous call's contents: clear what must start at zero

@@ -1,5 +1,5 @@
 """ctypes binding for libqsgw.so (include/qsgw.h). Argument marshalling only: every step of
-the computation runs in the library's CUDA kernels (or cuSOLVER for the FP64 Cholesky).
+the computation runs in the library's CUDA kernels.
 
 Functions keep the C names. Array arguments may be torch tensors (device or host), numpy
 arrays (host) or raw integer addresses. Any status other than QSGW_OK raises QsgwError.

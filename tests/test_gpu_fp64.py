@@ -147,6 +147,11 @@ def test_not_positive_definite_reports_info(N):
         assert info[0] > 0
     finally:
         N.qsgw_chi0_destroy(ctx)
+    # the index is that of the first non-positive pivot of a Cholesky factorisation of eps
+    d = oracle.delta(eps_occ(1, 0, 0, 8), eps_unocc(1, 0, 0, 32))[0]
+    chi = oracle.chi0_full(np.ascontiguousarray(zt.T), d, np.array(om), -2.0)
+    _, _, _, info_ref = oracle.eps_w(chi, np.full(n, 50.0), want_eps=False, want_wc=False)
+    assert info_ref[0] > 0 and list(info) == list(info_ref)
 
 
 def test_device_generator_matches_host_generator(N):
