@@ -7,7 +7,12 @@ tensor-core HERK), chi0 readout, eps, FP64 Cholesky inverse and W.
 
 Metric: algorithmic chi0 TFLOP/s, F = 4 K n_pb (n_pb + 1) L per step, over the whole step time
 (eps/W included), mixed precision (the default `--prec mixed`). The FP64 form is measured on a
-2-k-point sample of the same Z (GB300 FP64 runs at ~1 TFLOP/s) and reported beside it.
+2-k-point sample of the same Z (GB300 FP64 runs at ~1.2 TFLOP/s) and reported beside it.
+
+The default line (one GPU) also carries, each timed on its own after the medium steps, the
+largest configuration ("large": n_pb = 4000, 9.2M columns, 16 frequencies, one pass with Z drawn
+per k-point on the device) and the batched one ("batched": 24 uneven q-points, q-points/s, tile
+plan chosen by the library's autotuner).
 
 `--impl reference` times the FP64 CPU oracle (test infrastructure) on a bounded sample of the
 same workload, on the host cores.
@@ -268,12 +273,13 @@ def run_ours(args, rank, world, dev_index):
 
 
 # ------------------------------------------------------------------ batched uneven q-points
-def run_batched(args):
+def run_batched(args, steps=None, warmup=None):
     """24 q-points, n_pb ~ U{900..2200}, 32 k-points with n_unocc ~ U{250..600} per (q, k), 12
-    frequencies. Per k-point one qsgw_chi0_accumulate_batch call (24 blocks, one persistent launch);
-    then chi0 readout and eps/W for every q. The 24 x 32 blocks of Z (~320 GB) do not fit in HBM
-    together, so each k-point's Z is drawn on the device before its batch call, outside the
-    CUDA-event brackets that time the library calls."""
+    frequencies. Per k-point one qsgw_chi0_accumulate_batch call (24 blocks, one persistent launch,
+    the tile plan chosen by qsgw_chi0_autotune on the first k-point's blocks before the warm-up);
+    then eps/W for every q. The 24 x 32 blocks of Z (~320 GB) do not fit in HBM together, so each
+    k-point's Z is drawn on the device before its batch call, outside the CUDA-event brackets that
+    time the library calls. Returns the result as a dict."""
     import torch
     from paper_2506_03477_gb300 import native as N
     from synthetic import BATCHED as B
@@ -290,6 +296,16 @@ def run_batched(args):
     vq = [torch.from_numpy(coulomb_v(B.seed, q, npb[q])).to(dev) for q in range(B.n_q)]
     Wq = [torch.empty((B.n_omega, npb[q], npb[q]), dtype=torch.complex128, device=dev) for q in range(B.n_q)]
     events = []
+    steps = args.steps if steps is None else steps
+    warmup = max(1, min(args.warmup, 1)) if warmup is None else warmup
+    # autotune the tile plan on the first k-point's 24 blocks (scratch accumulators; not timed)
+    for q in range(B.n_q):
+        N.qsgw_synth_z(B.seed, q, 0, npb[q], B.n_occ, nu[q][0], B.s_div, Zq[q], npb[q], stream=stream)
+    torch.cuda.synchronize(dev)
+    t_tune = time.perf_counter()
+    plan, plan_ms = N.qsgw_chi0_autotune(ctx, [(q, Zq[q], npb[q], B.n_occ, nu[q][0], eo[q][0], eu[q][0])
+                                              for q in range(B.n_q)], reps=2)
+    t_tune = time.perf_counter() - t_tune
 
     def step(record):
         for q in range(B.n_q):
@@ -312,24 +328,34 @@ def run_batched(args):
         if record:
             events.append(("epsw", e0, e1))
 
-    for _ in range(max(1, min(args.warmup, 1))):
+    for _ in range(warmup):
         step(False)
     torch.cuda.synchronize(dev)
     with ClockSampler(0) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             step(True)
         torch.cuda.synchronize(dev)
     N.qsgw_chi0_destroy(ctx)
-    chi_ms = sum(a.elapsed_time(b) for n, a, b in events if n == "chi0") / args.steps
-    w_ms = sum(a.elapsed_time(b) for n, a, b in events if n == "epsw") / args.steps
+    del Zq, Wq
+    chi_ms = sum(a.elapsed_time(b) for n, a, b in events if n == "chi0") / steps
+    w_ms = sum(a.elapsed_time(b) for n, a, b in events if n == "epsw") / steps
     step_ms = chi_ms + w_ms
+    sustained = peaks()[0]
+    issued = sum(issued_mma_flops(npb[q], B.n_omega, B.n_occ * nu[q][k], plan[0])
+                 for q in range(B.n_q) for k in range(B.n_k))
     out = {"metric": "batched chi0+W: q-points/s (and algorithmic chi0 TFLOP/s)", "workload": B.name,
            "qpoints_per_s": B.n_q / (step_ms * 1e-3), "value": flops / (step_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
            "chi0_only_tflops": flops / (chi_ms * 1e-3) / 1e12, "ms_chi0_per_step": chi_ms, "ms_eps_w_per_step": w_ms,
-           "steps": args.steps, "flops_per_step": flops, "clocks": clk.summary(),
+           "steps": steps, "warmup": warmup, "flops_per_step": flops, "clocks": clk.summary(),
+           "tile_plan": {"tile_cols": plan[0], "tail_pieces": plan[1], "ms_per_launch_in_tuning": plan_ms,
+                         "tuning_s": t_tune},
+           "roofline": {"bound": "tensor", "achieved": flops / (chi_ms * 1e-3) / 1e12, "peak": sustained,
+                        "unit": "TFLOP/s", "frac": flops / (chi_ms * 1e-3) / 1e12 / sustained,
+                        "tensor_pipe_issued_tflops": issued / (chi_ms * 1e-3) / 1e12,
+                        "tensor_pipe_frac": issued / (chi_ms * 1e-3) / 1e12 / sustained},
            "note": "one persistent launch per k-point over all 24 q-points; Z drawn on the device between "
                    "the timed library calls (it does not fit in HBM at once)"}
-    print(json.dumps(out))
+    return out
 
 
 def run_large(args):
@@ -364,17 +390,22 @@ def run_large(args):
         ev[2].record(stream)
         torch.cuda.synchronize(dev)
     N.qsgw_chi0_destroy(ctx)
+    del W
     chi_ms, w_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     sustained = peaks()[0]
     issued = issued_mma_flops(n, Lg, no * nu) * G.n_k
     out = {"metric": "large streamed chi0 + W: algorithmic TFLOP/s", "workload": G.name,
            "value": flops / ((chi_ms + w_ms) * 1e-3) / 1e12, "unit": "TFLOP/s",
            "chi0_only_tflops": flops / (chi_ms * 1e-3) / 1e12,
-           "tensor_pipe_issued_tflops": issued / (chi_ms * 1e-3) / 1e12,
-           "tensor_pipe_frac": issued / (chi_ms * 1e-3) / 1e12 / sustained,
            "ms_chi0": chi_ms, "ms_eps_w": w_ms, "flops": flops, "clocks": clk.summary(),
-           "note": "one pass (64 k-points after a 1-k-point warm-up); Z drawn on the device inside the call"}
-    print(json.dumps(out))
+           "roofline": {"bound": "tensor", "achieved": flops / (chi_ms * 1e-3) / 1e12, "peak": sustained,
+                        "unit": "TFLOP/s", "frac": flops / (chi_ms * 1e-3) / 1e12 / sustained,
+                        "tensor_pipe_issued_tflops": issued / (chi_ms * 1e-3) / 1e12,
+                        "tensor_pipe_frac": issued / (chi_ms * 1e-3) / 1e12 / sustained},
+           "eps_inv_tflops": Lg * 4.0 * n ** 3 / (w_ms * 1e-3) / 1e12,
+           "note": "one pass (64 k-points after a 1-k-point warm-up); Z drawn on the device inside the call; "
+                   "eps_inv_tflops counts 4 n^3 real flops per frequency (Cholesky + inverse from the factor)"}
+    return out
 
 
 def run_sigx(args):
@@ -685,6 +716,8 @@ def main():
     ap.add_argument("--sigx-occ", type=int, default=276, help="occupied states per k-point for --workload sigx "
                     "(profiling aid; the workload uses 276)")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true", help="leave out the large and batched results of the "
+                    "default line")
     ap.add_argument("--workload", default="medium",
                     choices=["medium", "batched", "large", "sigx", "realaxis", "sigc"],
                     help="medium = the benchmark line; batched = the 24-q uneven workload (q-points/s); "
@@ -734,8 +767,10 @@ def main():
 
     if args.workload in ("batched", "large", "sigx", "realaxis", "sigc"):
         if rank == 0:
-            {"batched": run_batched, "large": run_large, "sigx": run_sigx, "realaxis": run_realaxis,
-             "sigc": run_sigc}[args.workload](args)
+            r = {"batched": run_batched, "large": run_large, "sigx": run_sigx, "realaxis": run_realaxis,
+                 "sigc": run_sigc}[args.workload](args)
+            if r is not None:
+                print(json.dumps(r))
         return
     res = run_ours(args, rank, world, local)
     if rank != 0:
@@ -770,12 +805,22 @@ def main():
         out["note"] = f"profiling case: {args.k_points} of {N_K} k-points per step (not a bench line)"
     if not args.skip_cpu and args.k_points == N_K:
         out["cpu_baseline"] = cpu_baseline(res["chi"])
+    if world == 1 and not args.skip_extra and args.k_points == N_K:
+        # the largest configuration and the batched one, each timed on its own after the medium line
+        import torch
+        del res
+        torch.cuda.empty_cache()
+        out["large"] = run_large(args)
+        torch.cuda.empty_cache()
+        out["batched"] = run_batched(args, steps=1, warmup=1)
     print(json.dumps(out))
 
 
-def issued_mma_flops(n_pb, n_omega, k_cols):
-    """BF16 MMA flops one accumulate call over k_cols columns issues (same tiling rules as the library)."""
-    TJ = next(t for t in range(min(256 // n_omega, 32), 0, -1) if (t * n_omega) % 16 == 0)
+def issued_mma_flops(n_pb, n_omega, k_cols, TJ=None):
+    """BF16 MMA flops one accumulate call over k_cols columns issues (same tiling rules as the library;
+    TJ = the tile plan's columns per tile, default the widest)."""
+    if not TJ:
+        TJ = next(t for t in range(min(256 // n_omega, 32), 0, -1) if (t * n_omega) % 16 == 0)
     n = TJ * n_omega
     n_pad = (n_pb + 63) // 64 * 64
     n_it, n_jt = n_pad // 64, (n_pb + TJ - 1) // TJ

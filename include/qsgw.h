@@ -132,10 +132,45 @@ typedef struct {
  * blocks must name distinct q (QSGW_ERR_ARG otherwise), at most 32 per call, all pointers on the
  * device. In QSGW_MIXED_BF16X3 every block's operands are prepared and then ONE persistent
  * tensor-core launch works through all (block, tile, chunk) items, balanced over the SMs, so
- * uneven n_pb and column counts share the GPU; in QSGW_FP64 the blocks run one after another.
+ * uneven n_pb and column counts share the GPU; in QSGW_FP64 ONE launch of the FP64 kernel covers
+ * all (block, tile, K-slice) items, each block cut into the slices the one-block call would use,
+ * so its result is bitwise that of qsgw_chi0_accumulate on the block alone.
  * The first call with a new set of shapes allocates scratch and tile lists; after such a warm-up
  * call the sequence contains only kernel launches and can be captured in a CUDA graph. */
 qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx *ctx, int n_blocks, const qsgw_block *blocks);
+
+/* ---- tile plans and the autotuner (Alg. 1 QKM blocks; the batching pattern of the mixed path) ----
+ * A tile plan of the tensor-core launch: J columns per output tile (0 = the widest one allowed,
+ * with N = tile_cols * n_omega <= 256 and a multiple of 16) and the number of chunk-range pieces
+ * each tile of a partial last wave is cut into (0 = enough pieces to fill the SMs, capped by the
+ * block's chunk count; 1 = not cut). Every plan gives the same result up to the order of the
+ * double-float additions (chunks are exact FP32 sums in every plan). */
+typedef struct {
+  int tile_cols;
+  int tail_pieces;
+} qsgw_tile_plan;
+
+/* The tuner's candidates for n_omega frequencies: the three widest valid tile widths, each with
+ * the default tail cut and with none. Writes at most max_out plans; returns how many. */
+int qsgw_tile_plan_candidates(int n_omega, qsgw_tile_plan *out, int max_out);
+
+/* Time every candidate plan on these blocks (as for qsgw_chi0_accumulate_batch: distinct q, device
+ * pointers) with CUDA events, reps launches each after one warm-up launch, into scratch
+ * accumulators of the blocks' sizes that are allocated for the call and freed after it, so the
+ * context's chi0 is untouched. The fastest plan is kept for the blocks' size class (n_omega, log2
+ * of the blocks' total 64 x 64 output-tile area, log2 of their largest chunk count of 1024
+ * columns), and later mixed accumulate calls of that class use it. When the environment variable
+ * QSGW_TUNE_CACHE names a file, the choice is appended to it, and qsgw_chi0_init of a mixed
+ * context reads the plans back from it. chosen and ms_chosen (nullable) receive the plan and its
+ * time per launch. QSGW_MIXED_BF16X3 chi0 contexts only (QSGW_ERR_STATE otherwise); QSGW_ERR_NOMEM
+ * if the scratch accumulators do not fit. Synchronises the stream. */
+qsgw_status qsgw_chi0_autotune(qsgw_ctx *ctx, int n_blocks, const qsgw_block *blocks, int reps,
+                               qsgw_tile_plan *chosen, float *ms_chosen);
+
+/* Use this plan for every later mixed accumulate call of the context (NULL: back to the tuned or
+ * default plan). QSGW_ERR_ARG for a tile width the frequency count does not allow. The I^c
+ * products keep the default width whatever is set. */
+qsgw_status qsgw_chi0_set_tile_plan(qsgw_ctx *ctx, const qsgw_tile_plan *plan);
 
 /* Write chi0(q) (the scaled, mirrored accumulator: full Hermitian, imaginary part of the
  * diagonal exactly zero) into chi0, device complex128 [n_omega][n_pb][n_pb]. Synchronises

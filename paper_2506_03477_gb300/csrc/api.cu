@@ -5,6 +5,8 @@
 // stacked products).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -157,6 +159,8 @@ qsgw_status take_device_error(qsgw_ctx* c) {
   return QSGW_OK;
 }
 
+void load_plans(qsgw_ctx* c);  // tuned tile plans from the plan file (defined with the autotuner calls)
+
 qsgw_status check_grid(const qsgw_ctx* c, int n_omega, const double* omega) {
   if (n_omega != c->g.L || !omega) return QSGW_ERR_ARG;
   for (int l = 0; l < n_omega; ++l)
@@ -256,6 +260,7 @@ qsgw_status qsgw_chi0_init(qsgw_ctx** out, int n_q, const int* n_pb, int n_omega
     qsgw_chi0_destroy(c);
     return st;
   }
+  if (prec == QSGW_MIXED_BF16X3) load_plans(c);
   *out = c;
   return QSGW_OK;
 }
@@ -466,10 +471,13 @@ qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx* c, int q, const void* Z, long lon
   return accumulate_any(c, q, Z, true, ldz, n_occ, n_pb, nullptr, v, 0, nullptr);
 }
 
-qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
+}  // extern "C"
+
+namespace {
+// Checks a batch of blocks (distinct q, device pointers) and describes them for the mixed kernels.
+qsgw_status batch_blocks(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks, MixedBlock* mb) {
   if (!c || n_blocks < 1 || n_blocks > 32 || !blocks) return QSGW_ERR_ARG;
   if (c->sigx || c->spectral || c->sigc) return QSGW_ERR_STATE;
-  MixedBlock mb[32];
   for (int i = 0; i < n_blocks; ++i) {
     const qsgw_block& b = blocks[i];
     if (b.q < 0 || b.q >= c->n_q || !b.Z || !b.eps_occ || !b.eps_unocc || b.n_occ < 1 || b.n_unocc < 1)
@@ -482,18 +490,129 @@ qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_blo
     mb[i] = MixedBlock{b.Z, b.ldz, a.n_pb, a.n_pad, b.n_occ, b.n_unocc, b.eps_occ,
                        b.eps_unocc, static_cast<float4*>(a.acc), /*z32*/ false, /*wv*/ nullptr};
   }
+  return QSGW_OK;
+}
+
+// Tuned plans persist in a text file named by QSGW_TUNE_CACHE, one line per size class:
+// "qsgw-plan <n_omega> <area class> <chunk class> <tile columns> <tail pieces>".
+void load_plans(qsgw_ctx* c) {
+  const char* path = std::getenv("QSGW_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    PlanEntry e{};
+    if (std::sscanf(line, "qsgw-plan %d %d %d %d %d", &e.L, &e.ca, &e.cc, &e.plan.tj, &e.plan.pieces) != 5) continue;
+    if (e.L != c->g.L || !mixed_plan_valid(e.L, e.plan)) continue;
+    bool found = false;
+    for (PlanEntry& x : c->mixed.plans)
+      if (x.L == e.L && x.ca == e.ca && x.cc == e.cc) {
+        x.plan = e.plan;  // the last line of a class wins
+        found = true;
+      }
+    if (!found) c->mixed.plans.push_back(e);
+  }
+  std::fclose(f);
+}
+
+void save_plan(int L, int ca, int cc, const TilePlan& p) {
+  const char* path = std::getenv("QSGW_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "qsgw-plan %d %d %d %d %d\n", L, ca, cc, p.tj, p.pieces);
+  std::fclose(f);
+}
+}  // namespace
+
+extern "C" {
+
+qsgw_status qsgw_chi0_accumulate_batch(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks) {
+  MixedBlock mb[32];
+  qsgw_status bst = batch_blocks(c, n_blocks, blocks, mb);
+  if (bst != QSGW_OK) return bst;
   if (c->prec == QSGW_FP64) {
+    // weights of every block, then ONE launch of the FP64 HERK over all (block, tile, slice) items
+    const int L = c->g.L;
+    size_t w_total = 0, part_total = 0;
+    int S[32];
+    for (int i = 0; i < n_blocks; ++i) {
+      const QAcc& a = c->q[blocks[i].q];
+      const long long K = (long long)blocks[i].n_occ * blocks[i].n_unocc;
+      S[i] = herk_fp64_slices(a.n_pad, L, K);
+      w_total += (size_t)K * L;
+      if (S[i] > 1) part_total += (size_t)S[i] * L * a.n_pad * a.n_pad;
+    }
+    qsgw_status st = grow(reinterpret_cast<void**>(&c->d_w), &c->w_cap, sizeof(double) * w_total);
+    if (st == QSGW_OK && part_total) st = grow(&c->d_part, &c->part_cap, sizeof(double2) * part_total);
+    if (st != QSGW_OK) return st;
+    Fp64Batch fb;
+    std::memset(&fb, 0, sizeof(fb));
+    fb.nb = n_blocks;
+    fb.L = L;
+    size_t w_off = 0, p_off = 0;
     for (int i = 0; i < n_blocks; ++i) {
       const qsgw_block& b = blocks[i];
-      qsgw_status st = accumulate_device(c, b.q, b.Z, false, b.ldz, b.n_occ, b.n_unocc,
-                                         b.eps_occ, b.eps_unocc);
-      if (st != QSGW_OK) return st;
+      const QAcc& a = c->q[b.q];
+      const long long K = (long long)b.n_occ * b.n_unocc;
+      double* w = c->d_w + w_off;
+      launch_weights_fp64(b.eps_occ, b.eps_unocc, b.n_occ, b.n_unocc, c->g, w, K, c->d_err, c->stream);
+      const int nt = a.n_pad / 64;
+      double2* part = S[i] > 1 ? static_cast<double2*>(c->d_part) + p_off : nullptr;
+      fb.b[i] = Fp64Blk{static_cast<const double2*>(b.Z), b.ldz, K, w, K, static_cast<double2*>(a.acc), part,
+                        a.n_pb, a.n_pad, S[i], fb.items};
+      fb.items += nt * (nt + 1) / 2 * S[i];
+      w_off += (size_t)K * L;
+      if (S[i] > 1) p_off += (size_t)S[i] * L * a.n_pad * a.n_pad;
     }
-    return QSGW_OK;
+    launch_herk_fp64_batch(fb, c->stream);
+    return cuda_status(cudaGetLastError());
   }
   qsgw_status st = mixed_accumulate_batch(c->mixed, n_blocks, mb, c->g, c->d_err, c->stream);
   if (st != QSGW_OK) return st;
   return cuda_status(cudaGetLastError());
+}
+
+int qsgw_tile_plan_candidates(int n_omega, qsgw_tile_plan* out, int max_out) {
+  if (!out || max_out < 1) return 0;
+  TilePlan cand[16];
+  const int n = std::min(mixed_plan_candidates(n_omega, cand, 16), max_out);
+  for (int i = 0; i < n; ++i) out[i] = qsgw_tile_plan{cand[i].tj, cand[i].pieces};
+  return n;
+}
+
+qsgw_status qsgw_chi0_set_tile_plan(qsgw_ctx* c, const qsgw_tile_plan* plan) {
+  if (!c) return QSGW_ERR_ARG;
+  if (c->prec != QSGW_MIXED_BF16X3) return QSGW_ERR_STATE;
+  if (!plan) {
+    c->mixed.use_forced = false;
+    return QSGW_OK;
+  }
+  const TilePlan p{plan->tile_cols, plan->tail_pieces};
+  if (!mixed_plan_valid(c->g.L, p)) return QSGW_ERR_ARG;
+  c->mixed.forced = p;
+  c->mixed.use_forced = true;
+  return QSGW_OK;
+}
+
+qsgw_status qsgw_chi0_autotune(qsgw_ctx* c, int n_blocks, const qsgw_block* blocks, int reps,
+                               qsgw_tile_plan* chosen, float* ms_chosen) {
+  MixedBlock mb[32];
+  qsgw_status st = batch_blocks(c, n_blocks, blocks, mb);
+  if (st != QSGW_OK) return st;
+  if (c->prec != QSGW_MIXED_BF16X3) return QSGW_ERR_STATE;
+  if (reps < 1 || reps > 100) return QSGW_ERR_ARG;
+  TilePlan best;
+  float ms = 0.f;
+  st = mixed_autotune(c->mixed, n_blocks, mb, c->g, c->d_err, c->stream, reps, &best, &ms);
+  if (st != QSGW_OK) return st;
+  int ca = 0, cc = 0;
+  mixed_plan_class(n_blocks, mb, &ca, &cc);
+  save_plan(c->g.L, ca, cc, best);
+  if (chosen) *chosen = qsgw_tile_plan{best.tj, best.pieces};
+  if (ms_chosen) *ms_chosen = ms;
+  return QSGW_OK;
 }
 
 qsgw_status qsgw_chi0_finalize(qsgw_ctx* c, int q, void* chi0) {

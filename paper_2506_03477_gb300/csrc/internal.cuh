@@ -38,6 +38,23 @@ int herk_fp64_slices(int n_pad, int L, long long K, int ti_end = 0, int tj0 = 0)
 void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,
                       long long ldw, int L, int S, double2* acc, double2* part, cudaStream_t s, int ti_end = 0,
                       int tj0 = 0);
+// Blocks of distinct q-points in one launch over all (block, upper tile, K-slice) items; block b
+// uses S = herk_fp64_slices(n_pad, L, K) slices (partials in part, reduced per block after the
+// launch), so each block's result is bitwise that of launch_herk_fp64 on it alone.
+struct Fp64Blk {
+  const double2* Z;
+  long long ldz, K;
+  const double* w;  // weights [l][r], leading dimension ldw
+  long long ldw;
+  double2* acc;
+  double2* part;  // S > 1: [S][L][n_pad][n_pad]
+  int n_pb, n_pad, S, item0;
+};
+struct Fp64Batch {
+  Fp64Blk b[32];
+  int nb, L, items;
+};
+void launch_herk_fp64_batch(const Fp64Batch& p, cudaStream_t s);
 
 // ---- shared epilogues (kernels_epsw.cu)
 // Accumulator formats: FP64 complex (double2 [l][J][I]) or double-float planes (float2 hi/lo [l][re|im][J][I]).

@@ -55,23 +55,15 @@ void launch_weights_given_fp64(const double* v, int period, long long K, double*
 constexpr int kT = 64;   // output tile (I and J)
 constexpr int kKS = 16;  // K-step (columns staged per iteration)
 
-// grid: x = J tile - tj0, y = I tile, z = frequency + L * K-slice. Tiles strictly below the diagonal
-// exit at once. With tj0 > 0 and fewer I tiles than J tiles the grid covers one off-diagonal block
-// of the output: rows of I tiles [0, gridDim.y), columns of J tiles [tj0, n_pad / 64). With S = 1 the tile is added to acc; with S > 1 (few output tiles) slice sk covers
-// columns [K sk / S, K (sk + 1) / S) and stores its tile into its own partial buffer part[sk], which
-// herk_fp64_reduce_kernel then adds to acc in slice order (deterministic).
-__global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
-                                                        int n_pad, long long K, const double* __restrict__ w,
-                                                        long long ldw, int L, int S, int tj0,
-                                                        double2* __restrict__ acc, double2* __restrict__ part) {
-  const int tj = blockIdx.x + tj0, ti = blockIdx.y, l = blockIdx.z % L, sk = blockIdx.z / L;
-  if (tj < ti) return;
-  const long long r_begin = K * sk / S, r_end = K * (sk + 1) / S;
+// One 64 x 64 output tile (I tile ti, J tile tj) of one frequency over columns [r_begin, r_end):
+// sum_r w[r] conj(Z[I, r]) Z[J, r], added to out (add) or stored into it.
+__device__ __forceinline__ void herk_fp64_tile(const double2* __restrict__ Z, long long ldz, int n_pb, int n_pad,
+                                               long long r_begin, long long r_end, const double* __restrict__ wl,
+                                               int ti, int tj, double2* __restrict__ out, bool add) {
   __shared__ double2 sA[kKS][kT];
   __shared__ double2 sB[kKS][kT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = ti * kT, j0 = tj * kT;
-  const double* wl = w + (long long)l * ldw;
 
   double cr[4][4], ci[4][4];
 #pragma unroll
@@ -119,19 +111,53 @@ __global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restric
         }
     }
   }
-  const size_t nn = (size_t)n_pad * n_pad;
-  double2* out = S == 1 ? acc + (size_t)l * nn : part + ((size_t)sk * L + l) * nn;
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int I = i0 + ty + 16 * p, J = j0 + tx + 16 * q;
       double2* o = out + (size_t)J * n_pad + I;
-      double2 v = S == 1 ? *o : make_double2(0.0, 0.0);
+      double2 v = add ? *o : make_double2(0.0, 0.0);
       v.x += cr[p][q];
       v.y += ci[p][q];
       *o = v;
     }
+}
+
+// grid: x = J tile - tj0, y = I tile, z = frequency + L * K-slice. Tiles strictly below the diagonal
+// exit at once. With tj0 > 0 and fewer I tiles than J tiles the grid covers one off-diagonal block
+// of the output: rows of I tiles [0, gridDim.y), columns of J tiles [tj0, n_pad / 64). With S = 1 the
+// tile is added to acc; with S > 1 (few output tiles) slice sk covers columns [K sk / S, K (sk + 1) / S)
+// and stores its tile into its own partial buffer part[sk], which herk_fp64_reduce_kernel then adds
+// to acc in slice order (deterministic).
+__global__ void __launch_bounds__(256) herk_fp64_kernel(const double2* __restrict__ Z, long long ldz, int n_pb,
+                                                        int n_pad, long long K, const double* __restrict__ w,
+                                                        long long ldw, int L, int S, int tj0,
+                                                        double2* __restrict__ acc, double2* __restrict__ part) {
+  const int tj = blockIdx.x + tj0, ti = blockIdx.y, l = blockIdx.z % L, sk = blockIdx.z / L;
+  if (tj < ti) return;
+  const size_t nn = (size_t)n_pad * n_pad;
+  double2* out = S == 1 ? acc + (size_t)l * nn : part + ((size_t)sk * L + l) * nn;
+  herk_fp64_tile(Z, ldz, n_pb, n_pad, K * sk / S, K * (sk + 1) / S, w + (long long)l * ldw, ti, tj, out, S == 1);
+}
+
+// Batch over blocks of distinct q-points in one launch: grid (items, frequency), item = (block,
+// upper-triangle tile, K-slice), each block with the slice count the one-block path would pick, so
+// the sums run in the same order and the result is bitwise that of one launch per block.
+__global__ void __launch_bounds__(256) herk_fp64_batch_kernel(const __grid_constant__ Fp64Batch p) {
+  const int l = blockIdx.y;
+  int b = 0;
+  while (b + 1 < p.nb && p.b[b + 1].item0 <= (int)blockIdx.x) ++b;
+  const Fp64Blk& B = p.b[b];
+  const int local = blockIdx.x - B.item0, sk = local % B.S, t = local / B.S;
+  int tj = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);  // upper tile (ti, tj), ti <= tj, by column
+  while ((tj + 1) * (tj + 2) / 2 <= t) ++tj;
+  while (tj * (tj + 1) / 2 > t) --tj;
+  const int ti = t - tj * (tj + 1) / 2;
+  const size_t nn = (size_t)B.n_pad * B.n_pad;
+  double2* out = B.S == 1 ? B.acc + (size_t)l * nn : B.part + ((size_t)sk * p.L + l) * nn;
+  herk_fp64_tile(B.Z, B.ldz, B.n_pb, B.n_pad, B.K * sk / B.S, B.K * (sk + 1) / B.S, B.w + (long long)l * B.ldw, ti,
+                 tj, out, B.S == 1);
 }
 
 // acc += sum over slices sk = 0 .. S-1 of part[sk], on the upper-triangle tiles; grid as the HERK
@@ -164,6 +190,18 @@ int herk_fp64_slices(int n_pad, int L, long long K, int ti_end, int tj0) {
   if (S > 16) S = 16;
   if (S > steps) S = steps > 0 ? steps : 1;
   return (int)S;
+}
+
+void launch_herk_fp64_batch(const Fp64Batch& p, cudaStream_t s) {
+  if (p.nb < 1 || p.items < 1) return;
+  herk_fp64_batch_kernel<<<dim3(p.items, p.L), 256, 0, s>>>(p);
+  for (int b = 0; b < p.nb; ++b) {
+    const Fp64Blk& B = p.b[b];
+    if (B.S > 1) {
+      const int nt = B.n_pad / kT;
+      herk_fp64_reduce_kernel<<<dim3(nt, nt, p.L), 256, 0, s>>>(B.n_pad, p.L, B.S, 0, B.part, B.acc);
+    }
+  }
 }
 
 void launch_herk_fp64(const double2* Z, long long ldz, int n_pb, int n_pad, long long K, const double* w,

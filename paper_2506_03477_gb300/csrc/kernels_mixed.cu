@@ -845,6 +845,47 @@ static int tile_width(int L) {
 
 int mixed_tile_cols(int L) { return L >= 1 && L <= kMaxOmega ? tile_width(L) : 0; }
 
+static bool tile_width_ok(int t, int L) {
+  return t >= 1 && t * L >= 16 && t * L <= 256 && (t * L) % 16 == 0 && main_smem_bytes(t * L, t, L) <= kSmemMax;
+}
+
+bool mixed_plan_valid(int L, const TilePlan& p) {
+  return L >= 1 && L <= kMaxOmega && (p.tj == 0 || tile_width_ok(p.tj, L)) && p.pieces >= 0 && p.pieces <= 64;
+}
+
+int mixed_plan_candidates(int L, TilePlan* out, int max_out) {
+  if (L < 1 || L > kMaxOmega) return 0;
+  int n = 0, widths = 0;
+  for (int t = 256 / L; t >= 1 && widths < 3; --t) {
+    if (!tile_width_ok(t, L)) continue;
+    ++widths;
+    for (int pieces : {0, 1})
+      if (n < max_out) out[n++] = TilePlan{t, pieces};
+  }
+  return n;
+}
+
+static int ilog2(long long x) {
+  int e = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++e;
+  }
+  return e;
+}
+
+void mixed_plan_class(int nb, const MixedBlock* in, int* ca, int* cc) {
+  long long area = 0;
+  long long ch = 1;
+  for (int b = 0; b < nb; ++b) {
+    area += (long long)(in[b].n_pad / TI) * (in[b].n_pad / TI);
+    const long long K = (long long)in[b].n_occ * in[b].n_unocc;
+    ch = std::max(ch, (K + CHR - 1) / CHR);
+  }
+  *ca = ilog2(std::max(1LL, area));
+  *cc = ilog2(ch);
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static bool herk_set_attributes() {
@@ -886,8 +927,25 @@ static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, int r
 
 qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in, const OmegaGrid& g, int* d_err,
                                    cudaStream_t stream) {
-  const int L = g.L, TJ = tile_width(L), N = TJ * L;
-  if (TJ < 1 || N < 16 || N > 256 || nb < 1 || nb > kMaxBlocks) return QSGW_ERR_ARG;
+  if (nb < 1 || nb > kMaxBlocks) return QSGW_ERR_ARG;
+  const int L = g.L;
+  // the tile plan: forced, tuned for this size class, or the default; launches over a restricted
+  // block (the I^c products, whose row offsets are multiples of the default width) keep the default
+  TilePlan plan;
+  bool restricted = false;
+  for (int b = 0; b < nb; ++b) restricted = restricted || in[b].rows_i > 0;
+  if (!restricted) {
+    if (s.use_forced) {
+      plan = s.forced;
+    } else if (!s.plans.empty()) {
+      int ca = 0, cc = 0;
+      mixed_plan_class(nb, in, &ca, &cc);
+      for (const PlanEntry& e : s.plans)
+        if (e.L == L && e.ca == ca && e.cc == cc) plan = e.plan;
+    }
+  }
+  const int TJ = plan.tj > 0 ? plan.tj : tile_width(L), N = TJ * L;
+  if (!tile_width_ok(TJ, L)) return QSGW_ERR_ARG;
   struct Plan {
     long long K;
     int n_ch, n_kb, n_it, n_jt;
@@ -1002,6 +1060,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   }
   int P = R > 0 ? G / R : 1;
   if (P < 1) P = 1;
+  if (plan.pieces > 0) P = plan.pieces;
   if (R > 0 && P > min_ch_tail) P = min_ch_tail;
   a.P = P;
   a.n_items = a.T_whole + R * P;
@@ -1153,6 +1212,76 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
     return QSGW_ERR_CUDA;
   if (h_err == DEV_DOMAIN) return QSGW_ERR_DOMAIN;
   if (h_err == DEV_TIMEOUT) return QSGW_ERR_TIMEOUT;
+  return QSGW_OK;
+}
+
+qsgw_status mixed_autotune(MixedScratch& s, int nb, const MixedBlock* in, const OmegaGrid& g, int* d_err,
+                           cudaStream_t stream, int reps, TilePlan* best, float* best_ms) {
+  if (nb < 1 || nb > kMaxBlocks || reps < 1) return QSGW_ERR_ARG;
+  for (int b = 0; b < nb; ++b)
+    if (in[b].rows_i > 0) return QSGW_ERR_ARG;
+  const int L = g.L;
+  std::vector<MixedBlock> blk(in, in + nb);
+  size_t total = 0;
+  std::vector<size_t> off(nb);
+  for (int b = 0; b < nb; ++b) {  // scratch accumulators of the blocks' own sizes
+    off[b] = total;
+    total += align256((size_t)blk[b].n_pad * blk[b].n_pad * L * 2 * sizeof(float4));
+  }
+  void* tmp = nullptr;
+  if (cudaMalloc(&tmp, total) != cudaSuccess) {
+    cudaGetLastError();
+    return QSGW_ERR_NOMEM;
+  }
+  for (int b = 0; b < nb; ++b) blk[b].acc = reinterpret_cast<float4*>(static_cast<uint8_t*>(tmp) + off[b]);
+  TilePlan cand[16];
+  const int nc = mixed_plan_candidates(L, cand, 16);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  qsgw_status st = QSGW_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = QSGW_ERR_CUDA;
+  const bool saved_use = s.use_forced;
+  const TilePlan saved = s.forced;
+  float bms = 0.f;
+  TilePlan bp;
+  for (int c = 0; c < nc && st == QSGW_OK; ++c) {
+    s.use_forced = true;
+    s.forced = cand[c];
+    st = mixed_accumulate_batch(s, nb, blk.data(), g, d_err, stream);  // warm-up: scratch, tile lists
+    if (st != QSGW_OK) break;
+    if (cudaEventRecord(e0, stream) != cudaSuccess) st = QSGW_ERR_CUDA;
+    for (int r = 0; r < reps && st == QSGW_OK; ++r) st = mixed_accumulate_batch(s, nb, blk.data(), g, d_err, stream);
+    if (st != QSGW_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = QSGW_ERR_CUDA;
+      break;
+    }
+    ms /= reps;
+    if (c == 0 || ms < bms) {
+      bms = ms;
+      bp = cand[c];
+    }
+  }
+  s.use_forced = saved_use;
+  s.forced = saved;
+  cudaStreamSynchronize(stream);
+  cudaFree(tmp);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st != QSGW_OK) return st;
+  if (nc == 0) return QSGW_ERR_ARG;
+  int ca = 0, cc = 0;
+  mixed_plan_class(nb, in, &ca, &cc);
+  bool found = false;
+  for (PlanEntry& e : s.plans)
+    if (e.L == L && e.ca == ca && e.cc == cc) {
+      e.plan = bp;
+      found = true;
+    }
+  if (!found) s.plans.push_back(PlanEntry{L, ca, cc, bp});
+  if (best) *best = bp;
+  if (best_ms) *best_ms = bms;
   return QSGW_OK;
 }
 

@@ -13,6 +13,18 @@ struct TileList {
   int n_pb, tj, rows_i, col0, count;
   int2* tiles;
 };
+// Tile plan of the tensor-core launch: J columns per output tile (0: the widest the frequency count
+// allows) and the chunk-range pieces each tile of a partial last wave is cut into (0: enough to fill
+// the SMs, capped by the chunk count; 1: not cut).
+struct TilePlan {
+  int tj = 0, pieces = 0;
+};
+// A tuned plan for one size class: frequency count, log2 of the 64 x 64 output-tile area of all
+// blocks, log2 of the largest chunk count.
+struct PlanEntry {
+  int L, ca, cc;
+  TilePlan plan;
+};
 struct MixedScratch {
   void* planes = nullptr;
   size_t planes_cap = 0;
@@ -20,6 +32,9 @@ struct MixedScratch {
   bool attr_set = false;
   int n_sm = 0;
   int* counter = nullptr;  // work-queue counter of the tensor-core launch
+  std::vector<PlanEntry> plans;  // tuned plans (qsgw_chi0_autotune or the plan file)
+  bool use_forced = false;       // qsgw_chi0_set_tile_plan: this plan for every unrestricted launch
+  TilePlan forced;
 };
 
 // One block of transition columns for one q-point. acc: the q-point's accumulator, a double-float
@@ -51,6 +66,15 @@ qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long
                              int n_unocc, const double* eo, const double* eu, const double* wv, const OmegaGrid& g,
                              float4* acc, int* d_err, cudaStream_t stream);
 void mixed_free(MixedScratch& s);
+// Candidate plans for L frequencies (at most max_out), the tuner's search space: the three widest
+// valid tile widths, each with the default tail cut and with no cut.
+int mixed_plan_candidates(int L, TilePlan* out, int max_out);
+bool mixed_plan_valid(int L, const TilePlan& p);
+void mixed_plan_class(int nb, const MixedBlock* in, int* ca, int* cc);
+// Times every candidate on these blocks (into scratch accumulators of the same sizes, so the
+// blocks' own accumulators are untouched), keeps the fastest for the blocks' class in s.plans.
+qsgw_status mixed_autotune(MixedScratch& s, int nb, const MixedBlock* in, const OmegaGrid& g, int* d_err,
+                           cudaStream_t stream, int reps, TilePlan* best, float* best_ms);
 // chi0 of one block of columns into `chi0` using only a fixed file-scope device array (no allocation).
 qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_occ, int n_unocc, const double* eo,
                                const double* eu, const OmegaGrid& g, double spin, double2* chi0, cudaStream_t stream);

@@ -33,6 +33,7 @@ EXPORTS = [
     "qsgw_sigx_init", "qsgw_sigx_accumulate", "qsgw_sigx_accumulate_c64", "qsgw_selftest_wait_timeout",
     "qsgw_spectral_init", "qsgw_spectral_accumulate", "qsgw_spectral_finalize", "qsgw_spectral_real_axis",
     "qsgw_sigc_init", "qsgw_sigc_accumulate", "qsgw_sigc_finalize",
+    "qsgw_tile_plan_candidates", "qsgw_chi0_autotune", "qsgw_chi0_set_tile_plan",
 ]
 
 
@@ -40,6 +41,11 @@ class qsgw_block(ctypes.Structure):
     """C struct qsgw_block (include/qsgw.h)."""
     _fields_ = [("q", ctypes.c_int), ("Z", ctypes.c_void_p), ("ldz", ctypes.c_longlong), ("n_occ", ctypes.c_int),
                 ("n_unocc", ctypes.c_int), ("eps_occ", ctypes.c_void_p), ("eps_unocc", ctypes.c_void_p)]
+
+
+class qsgw_tile_plan(ctypes.Structure):
+    """C struct qsgw_tile_plan (include/qsgw.h)."""
+    _fields_ = [("tile_cols", ctypes.c_int), ("tail_pieces", ctypes.c_int)]
 
 
 class QsgwError(RuntimeError):
@@ -85,6 +91,9 @@ def load():
         "qsgw_chi0_accumulate_synthetic": [_p, _i, _u64, _i, _i, _i, _i, P(_i), _p, _p, _d],
         "qsgw_chi0_accumulate_batch": [_p, _i, P(qsgw_block)],
         "qsgw_chi0_block_noalloc": [_p, _ll, _i, _i, _i, _p, _p, _i, P(_d), _d, _p, _p],
+        "qsgw_tile_plan_candidates": [_i, P(qsgw_tile_plan), _i],
+        "qsgw_chi0_autotune": [_p, _i, P(qsgw_block), _i, P(qsgw_tile_plan), P(ctypes.c_float)],
+        "qsgw_chi0_set_tile_plan": [_p, P(qsgw_tile_plan)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -267,6 +276,36 @@ def qsgw_chi0_accumulate_batch(ctx: int, blocks):
     for i, (q, Z, ldz, n_occ, n_unocc, eo, eu) in enumerate(blocks):
         arr[i] = qsgw_block(int(q), _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eo), _addr(eu))
     _check(load().qsgw_chi0_accumulate_batch(ctx, len(blocks), arr), "qsgw_chi0_accumulate_batch")
+
+
+def _block_array(blocks):
+    blocks = list(blocks)
+    arr = (qsgw_block * len(blocks))()
+    for i, (q, Z, ldz, n_occ, n_unocc, eo, eu) in enumerate(blocks):
+        arr[i] = qsgw_block(int(q), _addr(Z), int(ldz), int(n_occ), int(n_unocc), _addr(eo), _addr(eu))
+    return arr
+
+
+def qsgw_tile_plan_candidates(n_omega: int):
+    """The tuner's candidate plans for n_omega frequencies, as (tile_cols, tail_pieces) pairs."""
+    out = (qsgw_tile_plan * 16)()
+    n = load().qsgw_tile_plan_candidates(int(n_omega), out, 16)
+    return [(out[i].tile_cols, out[i].tail_pieces) for i in range(n)]
+
+
+def qsgw_chi0_autotune(ctx: int, blocks, reps: int = 2):
+    """Time every candidate plan on these blocks; returns ((tile_cols, tail_pieces), ms per launch)."""
+    arr = _block_array(blocks)
+    plan, ms = qsgw_tile_plan(), ctypes.c_float()
+    _check(load().qsgw_chi0_autotune(ctx, len(arr), arr, int(reps), ctypes.byref(plan), ctypes.byref(ms)),
+           "qsgw_chi0_autotune")
+    return (plan.tile_cols, plan.tail_pieces), ms.value
+
+
+def qsgw_chi0_set_tile_plan(ctx: int, plan):
+    """plan: (tile_cols, tail_pieces), or None for the tuned / default plan."""
+    p = None if plan is None else ctypes.byref(qsgw_tile_plan(int(plan[0]), int(plan[1])))
+    _check(load().qsgw_chi0_set_tile_plan(ctx, p), "qsgw_chi0_set_tile_plan")
 
 
 def qsgw_chi0_block_noalloc(Z, ldz: int, n_pb: int, n_occ: int, n_unocc: int, eps_occ, eps_unocc, omega,
