@@ -410,7 +410,7 @@ qsgw_status spectral_flush(qsgw_ctx* c, const std::vector<int>& js) {
 
 // ---- imaginary-axis correlation self-energy
 constexpr int kSigcRows = 4096;  // rows (band, target) of one batch of the product D
-constexpr int kSigcAlign = 128;  // row offset of the second row set: a multiple of every tile width
+constexpr int kSigcAlign = 256;  // row offset of the second row set: a multiple of the tile width at L = 1
 
 // The product of two row sets of a stacked operand Z (column-major, S rows, K columns): rows I <
 // rows_i against rows J >= col0, with weight 1, into accumulator q.

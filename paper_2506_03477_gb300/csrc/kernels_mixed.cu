@@ -27,7 +27,13 @@
 // (d1 d2 alone would be ~2^-20 of a typical product, which is why it is kept). After each chunk
 // both accumulators are stashed, and two drainer warps scale them by 2^-(eA+eB) (exact) and add
 // them into a double-float (2 x FP32) accumulator in global memory while the next chunk's MMAs
-// run; GB300's FP64 rate (~1 TFLOP/s) would make an FP64 read-modify-write here the bottleneck.
+// run; GB300's FP64 rate (~1.2 TFLOP/s) would make an FP64 read-modify-write here the bottleneck.
+//
+// Both operands' digits are formed once per call by the row preparation, as the exact
+// shared-memory image of each K-block: the A planes per 64-row I tile, the B planes (all
+// frequencies, scaled) per J tile. Every output tile of a J tile column reads the same B image, so
+// forming B in each CTA repeated the same digit arithmetic once per I tile; now the tensor-core
+// kernel only moves both images with bulk copies and issues the MMAs.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -45,10 +51,9 @@ constexpr int KB_PER_CH = CHR / KBR;      // 64
 constexpr int TI = 64;                    // rows I per tile (M = 128)
 constexpr int A_PLANE = 128 * KBK * 2;    // bytes of one digit plane of one A K-block (8 KB)
 constexpr int A_STAGE = 3 * A_PLANE;      // 24 KB
-constexpr int NS = 4;                     // load pipeline stages (A planes, raw column values, weights)
-constexpr int NSB = 2;                    // built-B stages (3 B stages with 3 load stages measured slower)
+constexpr int NS = 3;                     // pipeline stages: the A and B digit planes of one K-block each
 constexpr size_t kSmemMax = 227 * 1024;
-constexpr int NBG = 256;                  // B-operand / epilogue threads (warps 2..9)
+constexpr int NBG = 256;                  // epilogue threads (warps 2..9): chunk scales, TMEM -> stash
 constexpr int NDR = 64;                   // drainer threads (warps 10, 11): deferred accumulator updates
 constexpr int NTHREADS = 64 + NBG + NDR;
 constexpr uint32_t TMEM_L12 = 256;        // column of the level-1+2 accumulator
@@ -127,7 +132,8 @@ struct PrepColsBlk {
   const double* wv;  // non-null: given weights
   float* wst;        // [r][l] FP32 weights
   float* wmax;       // [chunk][l] their chunk maxima (the B-operand scale bound)
-  long long K;
+  long long K;       // columns of this launch
+  long long r0;      // block column of this launch's first column (the (n, m) index of column r0 + r)
   int n_unocc, n_ch;
 };
 struct PrepColsArgs {
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const __grid_cons
       const long long r = (long long)c * CHR + sub * PC_THREADS + t;
       float w = 0.f;
       if (r < K) {
-        const double x = B.wv[r % B.n_unocc];
+        const double x = B.wv[(B.r0 + r) % B.n_unocc];
         const bool ok = (x > 0.0) && isfinite(x);
         if (!ok) atomicCAS(p.d_err, DEV_OK, DEV_DOMAIN);
         w = ok ? (float)x : 0.f;
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const __grid_cons
     bool ok = false;
     float d = 0.f;
     if (r < K) {
-      const int n = (int)(r / B.n_unocc), m = (int)(r % B.n_unocc);
+      const int n = (int)((B.r0 + r) / B.n_unocc), m = (int)((B.r0 + r) % B.n_unocc);
       const double dd = B.eu[m] - B.eo[n];
       ok = (dd > 0.0) && isfinite(dd);
       if (!ok) atomicCAS(p.d_err, DEV_OK, DEV_DOMAIN);
@@ -208,25 +214,33 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const __grid_cons
 
 // ------------------------------------------------------------------ prep: rows
 // One CTA per (chunk, 64-row tile): chunk maximum of max(|Re z|, |Im z|) per row, its exponent,
-// the A-operand digit planes written as the exact shared-memory image of each K-block
-// ([plane][k-group 4][row-group 16][8 rows][8 K'] BF16, canonical no-swizzle K-major), and the
-// FP32 copy of Z laid out per J-tile and K-block ([jt][kb][16 r][TJ] float2) for the B side.
-// TZ: double2 (complex128 input) or float2 (complex64): every element is rounded to FP32 on load.
-// All blocks of one launch have the same TZ; grid (chunk, row tile, block), CTAs past a block's
-// chunk or row-tile count leave at once.
+// the A-operand digit planes of the row tile and the B-operand digit planes of the rows' J columns,
+// both written as the exact shared-memory image of each K-block (canonical no-swizzle K-major:
+// 16-byte rows of 8 K' values, 8-row core matrices 128 bytes apart), so the tensor-core kernel moves
+// each K-block with one bulk copy per operand.
+//   A image [plane][k-group 4][row-group 16][8 rows][8 K'] (rows: 64 Re rows (a, b), 64 Im rows (-b, a));
+//   B image of J tile jt [plane][k-group 4][n-group N/8][8 n][8 K'], n = l * TJ + j, values
+//     2^eB w_l(Delta_r) z_{J, r} (re, im pairs along K'), eB from max_r |w_l| * max_r |z_J| of the chunk.
+// Every CTA of a J tile column, and every I tile, reads the same B image, so the scaled digits of a
+// column are formed once per call rather than once per output tile. Rows past n_pad (J tiles reach
+// n_jt * TJ) get zero B digits. TZ: double2 (complex128 input) or float2 (complex64): every element
+// is rounded to FP32 on load. All blocks of one launch have the same TZ; grid (chunk, row tile,
+// block), CTAs past a block's chunk or row-tile count leave at once.
 struct PrepRowsBlk {
-  const void* Z;  // TZ [r][ldz]
+  const void* Z;  // TZ [r][ldz], at the launch's first column
   long long ldz, K;
   uint8_t* aplanes;
-  float2* braw;
+  uint8_t* bplanes;
+  const float* wst;   // [r][L] weights (prep_cols)
+  const float* wmax;  // [chunk][L] their chunk maxima
   float* zmax;
   int* expA;
-  int n_pb, n_pad, n_kb, n_jt, n_ch, n_it;
-  int a_rows, b_row0;  // rows I < a_rows need row digit planes, rows I >= b_row0 the column copy
+  int n_pb, n_pad, n_kb, n_jt, n_ch, n_it, n_itb;
+  int a_rows, b_row0;  // rows I < a_rows need row digit planes, rows I >= b_row0 column digit planes
 };
 struct PrepRowsArgs {
   PrepRowsBlk b[kMaxBlocks];
-  int TJ;
+  int TJ, L, N;
 };
 
 template <typename TZ>
@@ -234,14 +248,11 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
   __shared__ float red[4][TI];
   const PrepRowsBlk& B = p.b[blockIdx.z];
   const int c = blockIdx.x, it = blockIdx.y;
-  if (c >= B.n_ch || it >= B.n_it) return;
+  if (c >= B.n_ch || it >= B.n_itb) return;
   const TZ* __restrict__ Z = static_cast<const TZ*>(B.Z);
   const long long ldz = B.ldz, K = B.K;
-  const int n_pb = B.n_pb, n_pad = B.n_pad, n_kb = B.n_kb, n_jt = B.n_jt, TJ = p.TJ;
-  uint8_t* __restrict__ aplanes = B.aplanes;
-  float2* __restrict__ braw = B.braw;
-  float* __restrict__ zmax = B.zmax;
-  int* __restrict__ expA = B.expA;
+  const int n_pb = B.n_pb, n_pad = B.n_pad, n_kb = B.n_kb, n_jt = B.n_jt, TJ = p.TJ, L = p.L, N = p.N;
+  const int BPLANE = 64 * N, BSTAGE = 3 * BPLANE;
   const int il = threadIdx.x & (TI - 1), q = threadIdx.x >> 6;
   const int I = it * TI + il;
   const bool rowok = I < n_pb;
@@ -257,15 +268,20 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
   __syncthreads();
   m = fmaxf(fmaxf(red[0][il], red[1][il]), fmaxf(red[2][il], red[3][il]));
   const int eA = scale_exp(m);
-  if (q == 0) {
-    zmax[(size_t)c * n_pad + I] = m;
-    expA[(size_t)c * n_pad + I] = eA;
+  if (q == 0 && I < n_pad) {
+    B.zmax[(size_t)c * n_pad + I] = m;
+    B.expA[(size_t)c * n_pad + I] = eA;
   }
   const float sA = exp2i(eA);
   const int jt = I / TJ, jj = I % TJ;
-  const bool braw_ok = jt < n_jt && I >= B.b_row0;
-  const bool need_a = it * TI < B.a_rows;  // CTA-uniform: b_row0 is a multiple of the tile rows
-  if (!need_a && !(it * TI + TI > B.b_row0)) return;
+  const bool need_b = jt < n_jt && I >= B.b_row0;
+  // CTA-uniform: b_row0 is a multiple of the tile rows, and tiles past n_it carry B rows only
+  const bool need_a = it < B.n_it && it * TI < B.a_rows;
+  if (!need_a && !(it * TI + TI > B.b_row0 && it * TI < n_jt * TJ)) return;
+  float bsc[kMaxOmega];  // 2^eB of this column for every frequency (the kernel's epilogue uses 2^-eB)
+#pragma unroll
+  for (int l = 0; l < kMaxOmega; ++l)
+    bsc[l] = l < L ? exp2i(scale_exp(B.wmax[(size_t)c * L + l] * m)) : 0.f;
   for (int kbl = 0; kbl < KB_PER_CH; ++kbl) {
     const int kb = c * KB_PER_CH + kbl;
     float a[4], b[4];
@@ -276,30 +292,56 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
       if (rowok && r < K) z = Z[I + r * ldz];
       a[rr] = (float)z.x;
       b[rr] = (float)z.y;
-      if (braw_ok) braw[(((size_t)jt * n_kb + kb) * KBR + q * 4 + rr) * TJ + jj] = make_float2(a[rr], b[rr]);
     }
-    if (!need_a) continue;
-    float da[3][4], db[3][4];
+    if (need_a) {
+      float da[3][4], db[3][4];
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-      digits3(a[rr] * sA, da[0][rr], da[1][rr], da[2][rr]);
-      digits3(b[rr] * sA, db[0][rr], db[1][rr], db[2][rr]);
+      for (int rr = 0; rr < 4; ++rr) {
+        digits3(a[rr] * sA, da[0][rr], da[1][rr], da[2][rr]);
+        digits3(b[rr] * sA, db[0][rr], db[1][rr], db[2][rr]);
+      }
+      uint8_t* base = B.aplanes + ((size_t)it * n_kb + kb) * A_STAGE + q * 2048;
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl) {
+        uint4 re, im;  // Re row: (a, b) pairs; Im row: (-b, a) pairs
+        re.x = pack_bf16(da[pl][0], db[pl][0]);
+        re.y = pack_bf16(da[pl][1], db[pl][1]);
+        re.z = pack_bf16(da[pl][2], db[pl][2]);
+        re.w = pack_bf16(da[pl][3], db[pl][3]);
+        im.x = pack_bf16(-db[pl][0], da[pl][0]);
+        im.y = pack_bf16(-db[pl][1], da[pl][1]);
+        im.z = pack_bf16(-db[pl][2], da[pl][2]);
+        im.w = pack_bf16(-db[pl][3], da[pl][3]);
+        const int mre = il, mim = TI + il;
+        *reinterpret_cast<uint4*>(base + pl * A_PLANE + (mre >> 3) * 128 + (mre & 7) * 16) = re;
+        *reinterpret_cast<uint4*>(base + pl * A_PLANE + (mim >> 3) * 128 + (mim & 7) * 16) = im;
+      }
     }
-    uint8_t* base = aplanes + ((size_t)it * n_kb + kb) * A_STAGE + q * 2048;
+    if (need_b) {
+      const float* wr = B.wst + ((size_t)kb * KBR + q * 4) * L;  // this thread's 4 columns, every frequency
+      uint8_t* bb = B.bplanes + ((size_t)jt * n_kb + kb) * BSTAGE + q * 16 * N;
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      uint4 re, im;  // Re row: (a, b) pairs; Im row: (-b, a) pairs
-      re.x = pack_bf16(da[p][0], db[p][0]);
-      re.y = pack_bf16(da[p][1], db[p][1]);
-      re.z = pack_bf16(da[p][2], db[p][2]);
-      re.w = pack_bf16(da[p][3], db[p][3]);
-      im.x = pack_bf16(-db[p][0], da[p][0]);
-      im.y = pack_bf16(-db[p][1], da[p][1]);
-      im.z = pack_bf16(-db[p][2], da[p][2]);
-      im.w = pack_bf16(-db[p][3], da[p][3]);
-      const int mre = il, mim = TI + il;
-      *reinterpret_cast<uint4*>(base + p * A_PLANE + (mre >> 3) * 128 + (mre & 7) * 16) = re;
-      *reinterpret_cast<uint4*>(base + p * A_PLANE + (mim >> 3) * 128 + (mim & 7) * 16) = im;
+      for (int l = 0; l < kMaxOmega; ++l) {  // to the constant bound, so bsc stays in registers
+        if (l >= L) break;
+        float d[3][8];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          const float ww = wr[rr * L + l] * bsc[l];
+          digits3_mul(ww, a[rr], d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
+          digits3_mul(ww, b[rr], d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
+        }
+        const int n = l * TJ + jj;
+        uint8_t* dst = bb + (n >> 3) * 128 + (n & 7) * 16;
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+          uint4 v;
+          v.x = pack_bf16(d[pl][0], d[pl][1]);
+          v.y = pack_bf16(d[pl][2], d[pl][3]);
+          v.z = pack_bf16(d[pl][4], d[pl][5]);
+          v.w = pack_bf16(d[pl][6], d[pl][7]);
+          *reinterpret_cast<uint4*>(dst + pl * BPLANE) = v;
+        }
+      }
     }
   }
 }
@@ -308,8 +350,7 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
 // One block of transition columns (one accumulate request) for one q-point, as the kernel sees it.
 struct BlockDesc {
   const uint8_t* aplanes;
-  const float2* braw;
-  const float* wst;
+  const uint8_t* bplanes;
   const float* zmax;
   const int* expA;
   const float* wmax;
@@ -400,37 +441,35 @@ __device__ __forceinline__ void df_add(float2& v, float x) {
   v.y += e;
 }
 
-__host__ __device__ constexpr size_t main_smem_bytes(int N, int TJ, int L) {
-  return 1024 + (size_t)NS * A_STAGE + (size_t)NSB * 3 * 64 * N + (size_t)NS * KBR * TJ * 8 +
-         (size_t)NS * KBR * L * 4 + 256 * 4 * 2 + 32 * 8 + 64 + sizeof(BlockDesc) * kMaxBlocks +
-         sizeof(WorkItem) * kRing;
+// Bytes of the B digit planes of one K-block of one J tile (3 planes of N rows x 32 K' BF16).
+__host__ __device__ constexpr size_t b_stage_bytes(int N) { return (size_t)3 * 64 * N; }
+
+__host__ __device__ constexpr size_t main_smem_bytes(int N) {
+  return 1024 + (size_t)NS * (A_STAGE + b_stage_bytes(N)) + 256 * 4 * 2 + 32 * 8 + 64 +
+         sizeof(BlockDesc) * kMaxBlocks + sizeof(WorkItem) * kRing;
 }
 
-// 168 registers at most: the register file is split over the 4 SM sub-partitions and 10 warps
-// put 3 on some of them (3 * 32 * 168 <= 16384); __launch_bounds__ lets ptxas enforce it.
+// 168 registers at most: the register file is split over the 4 SM sub-partitions and 12 warps
+// put 3 on each of them (3 * 32 * 168 <= 16384); __launch_bounds__ lets ptxas enforce it.
 __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int N = p.N, TJ = p.TJ, L = p.L;
   const int BPLANE = 64 * N;  // bytes of one B digit plane of one K-block
   const int BSTAGE = 3 * BPLANE;
-  uint8_t* sA = smem;
-  uint8_t* sB = sA + NS * A_STAGE;
-  float2* sRaw = reinterpret_cast<float2*>(sB + NSB * BSTAGE);
-  float* sW = reinterpret_cast<float*>(sRaw + NS * KBR * TJ);
-  float* sScB = sW + NS * KBR * L;  // [2][256] 2^-eB per B column, by chunk parity
+  const int STAGE = A_STAGE + BSTAGE;  // a multiple of 1024 (N is a multiple of 16)
+  uint8_t* sStage = smem;              // [NS][A planes | B planes]
+  float* sScB = reinterpret_cast<float*>(sStage + NS * STAGE);  // [2][256] 2^-eB per B column, by chunk parity
   uint64_t* bars = reinterpret_cast<uint64_t*>(sScB + 512);
-  uint64_t* full = bars;             // [NS]   producer -> MMA, B-gen (bulk copies landed)
-  uint64_t* empty = full + NS;       // [NS]   MMA commit + 8 B-gen warps -> producer
-  uint64_t* bfull = empty + NS;      // [NSB]  8 B-gen warps -> MMA
-  uint64_t* bempty = bfull + NSB;    // [NSB]  MMA commit -> B-gen
-  uint64_t* accfull = bempty + NSB;  // MMA commit at chunk end -> epilogue
+  uint64_t* full = bars;             // [NS]   producer -> MMA and epilogue warps (bulk copies landed)
+  uint64_t* empty = full + NS;       // [NS]   MMA commit + 8 epilogue warps -> producer
+  uint64_t* accfull = empty + NS;    // MMA commit at chunk end -> epilogue
   uint64_t* accempty = accfull + 1;  // 8 epilogue warps -> MMA
   uint64_t* finbar = accempty + 1;
   uint64_t* stashed = finbar + 1;    // 8 epilogue warps -> drainers: a chunk end (stash or heartbeat)
   uint64_t* drained = stashed + 1;   // 2 drainer warps -> epilogue: that stash is in the accumulator
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
-  int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [2] builder-warp failure flags, by chunk parity
+  int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [2] epilogue-warp failure flags, by chunk parity
   int* sdesc = abortB + 2;  // [8] stash: kind (1 whole-tile chunk, 3 piece chunk, 2 end), block, it, jt, chunk,
                             //     parity, piece, first chunk of the piece
   BlockDesc* sBlk = reinterpret_cast<BlockDesc*>(bars + 32);  // block table, copied from the parameters
@@ -443,10 +482,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1 + NBG / 32);
-    }
-    for (int s = 0; s < NSB; ++s) {
-      mbar_init(&bfull[s], NBG / 32);
-      mbar_init(&bempty[s], 1);
     }
     mbar_init(accfull, 1);
     mbar_init(accempty, NBG / 32);
@@ -473,9 +508,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- producer: grabs items; bulk copies of A digit planes, raw B values, weights
+    // ---------------- producer: grabs items; bulk copies of the A and B digit planes of each K-block
     if (lane == 0) {
-      const uint32_t raw_bytes = KBR * TJ * 8, w_bytes = KBR * L * 4;
       int issued = 0, g = 0, pos = 0;
       WorkItem cur = ring[0];
       bool stop = cur.gt < 0;
@@ -491,10 +525,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             stop = true;
             break;
           }
-          mbar_arrive_expect_tx(&full[s], A_STAGE + raw_bytes + w_bytes);
-          bulk_g2s(sA + s * A_STAGE, bd.aplanes + ((size_t)tile.x * bd.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
-          bulk_g2s(sRaw + s * KBR * TJ, bd.braw + ((size_t)tile.y * bd.n_kb + kb) * KBR * TJ, raw_bytes, &full[s]);
-          bulk_g2s(sW + s * KBR * L, bd.wst + (size_t)kb * KBR * L, w_bytes, &full[s]);
+          uint8_t* st = sStage + s * STAGE;
+          mbar_arrive_expect_tx(&full[s], STAGE);
+          bulk_g2s(st, bd.aplanes + ((size_t)tile.x * bd.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
+          bulk_g2s(st + A_STAGE, bd.bplanes + ((size_t)tile.y * bd.n_kb + kb) * BSTAGE, BSTAGE, &full[s]);
           issued = g + 1;
         }
         if (stop || (cur.flags & 1)) break;
@@ -520,13 +554,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       while (!stop) {
         int nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
         for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
-          const int s = g % NS, sb = g % NSB, kbl = kbi % KB_PER_CH;
+          const int s = g % NS, kbl = kbi % KB_PER_CH;
           bool ok = mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
           if (ok && kbi == 0 && pos > 0) {  // the item was published before this K-block's copies
             cur = ring[pos % kRing];
             nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
           }
-          ok = ok && mbar_wait_bounded(&bfull[sb], (g / NSB) & 1, kWaitNs);
           if (ok && kbl == 0 && lc > 0) ok = mbar_wait_bounded(accempty, (lc - 1) & 1, kWaitNs);
           if (!ok) {
             atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
@@ -535,7 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           }
           if (kbl == 0) ++lc;
           tc_fence_after();
-          const uint32_t a_base = smem_u32(sA + s * A_STAGE), b_base = smem_u32(sB + sb * BSTAGE);
+          const uint32_t a_base = smem_u32(sStage + s * STAGE), b_base = a_base + A_STAGE;
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             const uint32_t ao = a_base + ks * 4096, bo = b_base + ks * 32 * N;
@@ -556,7 +589,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             mma_bf16(tmem + TMEM_L12, a2, b1, idesc, 1u);
           }
           mma_commit(&empty[s]);
-          mma_commit(&bempty[sb]);
           if (kbl == KB_PER_CH - 1 || kbi == nkb - 1) mma_commit(accfull);  // an item ends a chunk
         }
         if (stop || (cur.flags & 1)) break;
@@ -567,22 +599,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       mbar_wait_bounded(finbar, 0, kWaitNs);
     }
   } else if (warp < 2 + NBG / 32) {
-    // ---------------- B operand generation (scaled digits, all frequencies) + chunk epilogue
+    // ---------------- epilogue warps: the chunk's B scales for the drainers + the chunk epilogue.
+    // They follow the K-blocks (wait on full, arrive on empty) only to read the item ring in step
+    // with the producer and to keep the stages' phases from running ahead of them.
     const int bt = tid - 64;
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
     const int wg = (warp - 2) >> 2;           // column half handled in the epilogue
     const int m_row = quarter * 32 + lane;    // accumulator lane = A row
-    const int part = m_row / TI;
-    // B-operand row owned by this thread for the whole kernel (threads without one only flush).
-    // With N <= 128 (few frequencies) two threads share a row, each building 8 of its 16 K rows
-    // (K-groups 2 kh and 2 kh + 1), so all builder warps work.
-    const bool split = N <= NBG / 2;
-    const bool has_row = bt < (split ? 2 * N : N);
-    const int bn = has_row ? (split ? bt % N : bt) : 0, bl = bn / TJ, bj = bn % TJ;
-    const int kh = split ? bt / N : -1;  // K half built by this thread (-1: all four K-groups)
-    const int boff = (bn >> 3) * 128 + (bn & 7) * 16;
-    float bsc = 0.f;
-    bool bjok = false;
+    const bool has_col = bt < N;              // B column n = bt (frequency bl, tile column bj)
+    const int bl = bt / TJ, bj = bt % TJ;
     int it = 0, jt = 0, b = 0;
     // Deferred flush. At a chunk end of a whole tile the epilogue stores the two scaled
     // accumulator levels to this CTA's scratch (plain stores, no loads), frees TMEM and hands the
@@ -594,7 +619,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     int ns = 0;  // chunk ends announced
     bool ddead = false;
     // A warp whose wait timed out ("dead", warp-uniform) skips waits and work for the rest of its
-    // chunk and sets abortB[chunk parity]; at that chunk's epilogue barrier every builder warp reads
+    // chunk and sets abortB[chunk parity]; at that chunk's epilogue barrier every epilogue warp reads
     // the flag and all leave together, so no named barrier is ever left short of a warp. (Items end
     // on chunk boundaries, so no warp reads the item ring after a failure.)
     bool dead = false;
@@ -604,9 +629,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     while (more) {
       int nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
       for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
-        const int s = g % NS, sb = g % NSB, kbl = kbi % KB_PER_CH;
+        const int s = g % NS, kbl = kbi % KB_PER_CH;
         bool ok = !dead && mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
-        if (ok && g >= NSB) ok = mbar_wait_bounded(&bempty[sb], ((g / NSB) - 1) & 1, kWaitNs);
         if (!dead && __any_sync(0xffffffffu, !ok)) {
           dead = true;
           if (lane == 0) {
@@ -621,49 +645,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           const int2 tile = sBlk[b].tiles[cur.gt - sBlk[b].tile_off];
           it = tile.x;
           jt = tile.y;
-          bjok = has_row && (jt * TJ + bj < sBlk[b].n_pb);
         }
         const BlockDesc& bd = sBlk[b];
         const int c = cur.c0 + kbi / KB_PER_CH;
-        if (kbl == 0 && has_row) {  // B scale of this chunk: 2^eB from max_r |w_l| * max_r |z_J|
-          const float zm = bjok ? bd.zmax[(size_t)c * bd.n_pad + jt * TJ + bj] : 0.f;
-          const int e = scale_exp(bd.wmax[c * L + bl] * zm);
-          if (kh <= 0) sScB[(lc & 1) * 256 + bn] = exp2i(-e);
-          bsc = exp2i(e);
+        if (kbl == 0 && has_col) {  // 2^-eB of this chunk, the inverse of the scale the prep applied
+          const int J = jt * TJ + bj;
+          const float zm = J < bd.n_pb ? bd.zmax[(size_t)c * bd.n_pad + J] : 0.f;
+          sScB[(lc & 1) * 256 + bt] = exp2i(-scale_exp(bd.wmax[c * L + bl] * zm));
         }
-        if (has_row && !dead) {
-          const float2* raw = sRaw + s * KBR * TJ + bj;
-          const float* ws = sW + s * KBR * L + bl;
-          uint8_t* bdst = sB + sb * BSTAGE + boff;
-#pragma unroll
-          for (int kg = 0; kg < 4; ++kg) {
-            if (kh >= 0 && (kg >> 1) != kh) continue;
-            float d[3][8];
-#pragma unroll
-            for (int rr = 0; rr < 4; ++rr) {
-              const int rl = kg * 4 + rr;
-              const float2 z = bjok ? raw[rl * TJ] : make_float2(0.f, 0.f);
-              const float ww = ws[rl * L] * bsc;
-              digits3_mul(ww, z.x, d[0][2 * rr], d[1][2 * rr], d[2][2 * rr]);
-              digits3_mul(ww, z.y, d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
-            }
-#pragma unroll
-            for (int pl = 0; pl < 3; ++pl) {
-              uint4 v;
-              v.x = pack_bf16(d[pl][0], d[pl][1]);
-              v.y = pack_bf16(d[pl][2], d[pl][3]);
-              v.z = pack_bf16(d[pl][4], d[pl][5]);
-              v.w = pack_bf16(d[pl][6], d[pl][7]);
-              *reinterpret_cast<uint4*>(bdst + pl * BPLANE + kg * 16 * N) = v;
-            }
-          }
-        }
-        fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0 && !dead) {
-          mbar_arrive(&bfull[sb]);
-          mbar_arrive(&empty[s]);
-        }
+        if (lane == 0 && !dead) mbar_arrive(&empty[s]);
         if (kbl == KB_PER_CH - 1 || kbi == nkb - 1) {
           // ------------- chunk epilogue: TMEM -> registers -> scaled -> global accumulator
           ok = !dead && mbar_wait_bounded(accfull, lc & 1, kWaitNs);
@@ -834,20 +825,19 @@ __global__ void __launch_bounds__(256) piece_reduce_kernel(MainArgs p) {
 }
 
 // ------------------------------------------------------------------ host side
-// J columns per tile: the widest TJ with N = TJ * L <= 256, N % 16 == 0 (MMA shape rule for
-// M = 128) and the kernel's shared memory (raw-operand stages grow with TJ) within the limit.
-// L = 12: 20, L = 16: 16, L = 1: 128.
+// J columns per tile: the widest TJ with N = TJ * L <= 256 and N % 16 == 0 (MMA shape rule for
+// M = 128), within the kernel's shared memory. L = 12: 20, L = 16: 16, L = 1: 256.
+static bool tile_width_ok(int t, int L) {
+  return t >= 1 && t * L >= 16 && t * L <= 256 && (t * L) % 16 == 0 && main_smem_bytes(t * L) <= kSmemMax;
+}
+
 static int tile_width(int L) {
   for (int t = 256 / L; t >= 1; --t)
-    if ((t * L) % 16 == 0 && main_smem_bytes(t * L, t, L) <= kSmemMax) return t;
+    if (tile_width_ok(t, L)) return t;
   return 0;
 }
 
 int mixed_tile_cols(int L) { return L >= 1 && L <= kMaxOmega ? tile_width(L) : 0; }
-
-static bool tile_width_ok(int t, int L) {
-  return t >= 1 && t * L >= 16 && t * L <= 256 && (t * L) % 16 == 0 && main_smem_bytes(t * L, t, L) <= kSmemMax;
-}
 
 bool mixed_plan_valid(int L, const TilePlan& p) {
   return L >= 1 && L <= kMaxOmega && (p.tj == 0 || tile_width_ok(p.tj, L)) && p.pieces >= 0 && p.pieces <= 64;
@@ -893,7 +883,9 @@ static bool herk_set_attributes() {
          cudaSuccess;
 }
 
-// Device list of the tiles on or above the diagonal for one (n_pb, TJ), cached in the scratch.
+// Device list of the tiles on or above the diagonal for one (n_pb, TJ), cached in the scratch. The
+// order is column-major (J tile outer), so the CTAs that run at the same time share J tiles and
+// read each B image from L2 rather than HBM.
 static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, int rows_i, int col0, const int2** out,
                              int* count) {
   for (auto& e : s.tile_lists)
@@ -905,11 +897,11 @@ static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, int r
   std::vector<int2> tl;
   const int n_it = n_pad / TI, n_jt = (n_pb + TJ - 1) / TJ;
   if (rows_i > 0) {  // the off-diagonal block: I tiles covering rows [0, rows_i), J tiles from col0
-    for (int it = 0; it * TI < rows_i; ++it)
-      for (int jt = col0 / TJ; jt < n_jt; ++jt) tl.push_back(make_int2(it, jt));
+    for (int jt = col0 / TJ; jt < n_jt; ++jt)
+      for (int it = 0; it * TI < rows_i; ++it) tl.push_back(make_int2(it, jt));
   } else {
-    for (int it = 0; it < n_it; ++it)
-      for (int jt = 0; jt < n_jt; ++jt)
+    for (int jt = 0; jt < n_jt; ++jt)
+      for (int it = 0; it < n_it; ++it)
         if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) tl.push_back(make_int2(it, jt));
   }
   if (tl.empty()) return QSGW_ERR_ARG;
@@ -923,6 +915,146 @@ static qsgw_status tile_list(MixedScratch& s, int n_pb, int n_pad, int TJ, int r
   *out = d;
   *count = (int)tl.size();
   return QSGW_OK;
+}
+
+// One block's shape within one launch (K: the launch's columns of the block) and its scratch.
+struct Geom {
+  long long K;
+  int n_ch, n_kb, n_it, n_jt, n_itb;
+};
+static Geom geom_of(int n_pb, int n_pad, long long K, int TJ) {
+  Geom G;
+  G.K = K;
+  G.n_ch = (int)((K + CHR - 1) / CHR);
+  G.n_kb = G.n_ch * KB_PER_CH;
+  G.n_it = n_pad / TI;
+  G.n_jt = (n_pb + TJ - 1) / TJ;
+  G.n_itb = (std::max(n_pad, G.n_jt * TJ) + TI - 1) / TI;  // row tiles of the prep: A rows and B rows
+  return G;
+}
+static size_t geom_bytes(const Geom& G, int n_pad, int N, int L) {
+  return align256((size_t)G.n_it * G.n_kb * A_STAGE) + align256((size_t)G.n_jt * G.n_kb * b_stage_bytes(N)) +
+         align256((size_t)G.n_kb * KBR * L * sizeof(float)) + 2 * align256((size_t)G.n_ch * n_pad * sizeof(float)) +
+         align256((size_t)G.n_ch * L * sizeof(float));
+}
+struct Carve {
+  uint8_t* a;
+  uint8_t* b;
+  float* w;
+  float* zmax;
+  int* expA;
+  float* wmax;
+};
+static Carve carve(uint8_t* base, const Geom& G, int n_pad, int N, int L) {
+  Carve c;
+  size_t o = 0;
+  c.a = base + o;
+  o += align256((size_t)G.n_it * G.n_kb * A_STAGE);
+  c.b = base + o;
+  o += align256((size_t)G.n_jt * G.n_kb * b_stage_bytes(N));
+  c.w = reinterpret_cast<float*>(base + o);
+  o += align256((size_t)G.n_kb * KBR * L * sizeof(float));
+  c.zmax = reinterpret_cast<float*>(base + o);
+  o += align256((size_t)G.n_ch * n_pad * sizeof(float));
+  c.expA = reinterpret_cast<int*>(base + o);
+  o += align256((size_t)G.n_ch * n_pad * sizeof(float));
+  c.wmax = reinterpret_cast<float*>(base + o);
+  return c;
+}
+
+// One launch sequence over nb blocks, each with Z at the launch's first column (block column r0[b])
+// and its shape and scratch: prep_cols, prep_rows (A and B digit planes), the persistent
+// tensor-core kernel over all (block, tile, chunk) items, and the ordered reduction of the pieces of
+// split tiles. grid_cap: CTAs at most (and flush-scratch slots in fscr / pbuf).
+static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* r0, const Geom* G, const Carve* S,
+                                 const int2* const* tiles, const int* n_tiles, const OmegaGrid& g, int TJ, int pieces,
+                                 int grid_cap, float2* fscr, float2* pbuf, int* counter, int* d_err,
+                                 cudaStream_t stream) {
+  const int L = g.L, N = TJ * L;
+  MainArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nb = nb;
+  a.L = L;
+  a.TJ = TJ;
+  a.N = N;
+  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
+  a.d_err = d_err;
+  a.fscr = fscr;
+  a.pbuf = pbuf;
+  a.counter = counter;
+  PrepColsArgs pc;
+  std::memset(&pc, 0, sizeof(pc));
+  pc.g = g;
+  pc.d_err = d_err;
+  PrepRowsArgs pr[2];  // [0]: complex128 Z, [1]: complex64
+  std::memset(pr, 0, sizeof(pr));
+  for (int t = 0; t < 2; ++t) {
+    pr[t].TJ = TJ;
+    pr[t].L = L;
+    pr[t].N = N;
+  }
+  int T = 0, min_ch_tail = 1 << 30;
+  int nr[2] = {0, 0}, max_it[2] = {0, 0}, max_chr[2] = {0, 0}, max_ch = 0;
+  for (int b = 0; b < nb; ++b) {
+    const MixedBlock& B = in[b];
+    BlockDesc& d = a.blk[b];
+    d.aplanes = S[b].a;
+    d.bplanes = S[b].b;
+    d.zmax = S[b].zmax;
+    d.expA = S[b].expA;
+    d.wmax = S[b].wmax;
+    d.tiles = tiles[b];
+    d.n_tiles = n_tiles[b];
+    d.acc = reinterpret_cast<float2*>(B.acc);
+    d.acc2 = reinterpret_cast<double*>(d.acc + (size_t)L * 2 * B.n_pad * B.n_pad);
+    d.tile_off = T;
+    d.n_pb = B.n_pb;
+    d.n_pad = B.n_pad;
+    d.n_kb = G[b].n_kb;
+    d.n_kbr = (int)((G[b].K + KBR - 1) / KBR);
+    d.n_ch = G[b].n_ch;
+    T += d.n_tiles;
+    pc.b[b] = PrepColsBlk{B.eo, B.eu, B.wv, S[b].w, S[b].wmax, G[b].K, r0[b], B.n_unocc, G[b].n_ch};
+    const int t = B.z32 ? 1 : 0;
+    pr[t].b[nr[t]++] = PrepRowsBlk{B.Z, B.ldz, G[b].K, S[b].a, S[b].b, S[b].w, S[b].wmax, S[b].zmax, S[b].expA,
+                                   B.n_pb, B.n_pad, G[b].n_kb, G[b].n_jt, G[b].n_ch, G[b].n_it, G[b].n_itb,
+                                   B.rows_i > 0 ? B.rows_i : B.n_pad, B.rows_i > 0 ? B.col0 : 0};
+    max_ch = std::max(max_ch, G[b].n_ch);
+    max_chr[t] = std::max(max_chr[t], G[b].n_ch);
+    max_it[t] = std::max(max_it[t], G[b].n_itb);
+  }
+  prep_cols_kernel<<<dim3(max_ch, nb), PC_THREADS, 0, stream>>>(pc);
+  if (nr[0] > 0) prep_rows_kernel<double2><<<dim3(max_chr[0], max_it[0], nr[0]), 256, 0, stream>>>(pr[0]);
+  if (nr[1] > 0) prep_rows_kernel<float2><<<dim3(max_chr[1], max_it[1], nr[1]), 256, 0, stream>>>(pr[1]);
+  // whole tiles first; the last R tiles (a partial last wave) are split into P chunk ranges
+  const int Gc = grid_cap;
+  const int R = T >= Gc ? T % Gc : T;
+  a.T = T;
+  a.T_whole = T - R;
+  for (int b = 0; b < nb; ++b) {  // smallest chunk count among blocks that own tail tiles
+    const BlockDesc& d = a.blk[b];
+    if (d.tile_off + d.n_tiles > a.T_whole && d.n_ch < min_ch_tail) min_ch_tail = d.n_ch;
+  }
+  int P = R > 0 ? Gc / R : 1;
+  if (P < 1) P = 1;
+  if (pieces > 0) P = pieces;
+  if (R > 0 && P > min_ch_tail) P = min_ch_tail;
+  a.P = P;
+  a.n_items = a.T_whole + R * P;
+  if (cudaMemsetAsync(counter, 0, sizeof(int), stream) != cudaSuccess) return QSGW_ERR_CUDA;
+  const int grid = a.n_items < Gc ? a.n_items : Gc;
+  herk_mixed_kernel<<<grid, NTHREADS, main_smem_bytes(N), stream>>>(a);
+  if (R > 0) piece_reduce_kernel<<<dim3(R, (N * 128 + 255) / 256), 256, 0, stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
+}
+
+// B digit planes of one launch at most: a call whose planes would exceed it runs as launches over
+// chunk ranges (every launch covers the same chunks of every block; each chunk is flushed into the
+// accumulator anyway, so the cut changes nothing but the launch count).
+constexpr size_t kBPlaneBudget = 8ull << 30;
+
+static const void* advance_cols(const void* Z, bool z32, long long ldz, long long r0) {
+  return static_cast<const uint8_t*>(Z) + (size_t)r0 * ldz * (z32 ? sizeof(float2) : sizeof(double2));
 }
 
 qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in, const OmegaGrid& g, int* d_err,
@@ -946,41 +1078,38 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   }
   const int TJ = plan.tj > 0 ? plan.tj : tile_width(L), N = TJ * L;
   if (!tile_width_ok(TJ, L)) return QSGW_ERR_ARG;
-  struct Plan {
-    long long K;
-    int n_ch, n_kb, n_it, n_jt;
-    size_t o_a, o_raw, o_w, o_zmax, o_exp, o_wmax;
-  };
   if (s.n_sm == 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&s.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return QSGW_ERR_CUDA;
   }
-  std::vector<Plan> pl(nb);
-  const size_t fscr_bytes = align256((size_t)s.n_sm * kFscrPerCta * sizeof(float2));
-  size_t total = 2 * fscr_bytes;  // flush scratch, then the piece partial buffers
-  for (int b = 0; b < nb; ++b) {
-    Plan& P = pl[b];
-    const MixedBlock& B = in[b];
-    P.K = (long long)B.n_occ * B.n_unocc;
-    P.n_ch = (int)((P.K + CHR - 1) / CHR);
-    P.n_kb = P.n_ch * KB_PER_CH;
-    P.n_it = B.n_pad / TI;
-    P.n_jt = (B.n_pb + TJ - 1) / TJ;
-    P.o_a = total;
-    total += align256((size_t)P.n_it * P.n_kb * A_STAGE);
-    P.o_raw = total;
-    total += align256((size_t)P.n_jt * P.n_kb * KBR * TJ * sizeof(float2));
-    P.o_w = total;
-    total += align256((size_t)P.n_kb * KBR * L * sizeof(float));
-    P.o_zmax = total;
-    total += align256((size_t)P.n_ch * B.n_pad * sizeof(float));
-    P.o_exp = total;
-    total += align256((size_t)P.n_ch * B.n_pad * sizeof(int));
-    P.o_wmax = total;
-    total += align256((size_t)P.n_ch * L * sizeof(float));
+  if (!s.attr_set) {
+    if (!herk_set_attributes()) return QSGW_ERR_CUDA;
+    s.attr_set = true;
   }
+  const int2* tiles[kMaxBlocks];
+  int n_tiles[kMaxBlocks];
+  long long Kb[kMaxBlocks];
+  int max_ch = 0;
+  size_t b_per_chunk = 0;  // B digit-plane bytes of one chunk of every block
+  for (int b = 0; b < nb; ++b) {
+    const MixedBlock& B = in[b];
+    if (B.rows_i > 0 && (B.col0 % TJ != 0 || B.col0 < B.rows_i || B.col0 >= B.n_pb)) return QSGW_ERR_ARG;
+    qsgw_status st = tile_list(s, B.n_pb, B.n_pad, TJ, B.rows_i, B.col0, &tiles[b], &n_tiles[b]);
+    if (st != QSGW_OK) return st;
+    Kb[b] = (long long)B.n_occ * B.n_unocc;
+    max_ch = std::max(max_ch, (int)((Kb[b] + CHR - 1) / CHR));
+    b_per_chunk += (size_t)((B.n_pb + TJ - 1) / TJ) * KB_PER_CH * b_stage_bytes(N);
+  }
+  int cpl = max_ch;  // chunks per launch
+  if ((size_t)cpl * b_per_chunk > kBPlaneBudget) cpl = std::max(1, (int)(kBPlaneBudget / b_per_chunk));
+  // scratch: flush areas, then the blocks' planes for the first (largest) launch
+  const size_t fscr_bytes = align256((size_t)s.n_sm * kFscrPerCta * sizeof(float2));
+  size_t total = 2 * fscr_bytes;
+  for (int b = 0; b < nb; ++b)
+    total += geom_bytes(geom_of(in[b].n_pb, in[b].n_pad, std::min(Kb[b], (long long)cpl * CHR), TJ), in[b].n_pad, N,
+                        L);
   if (s.planes_cap < total) {
     if (s.planes) cudaFree(s.planes);
     s.planes = nullptr;
@@ -988,89 +1117,37 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     if (cudaMalloc(&s.planes, total) != cudaSuccess) return QSGW_ERR_NOMEM;
     s.planes_cap = total;
   }
-  if (!s.attr_set) {
-    if (!herk_set_attributes()) return QSGW_ERR_CUDA;
-    s.attr_set = true;
-  }
-  MainArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.nb = nb;
-  a.L = L;
-  a.TJ = TJ;
-  a.N = N;
-  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
-  a.d_err = d_err;
-  uint8_t* base = static_cast<uint8_t*>(s.planes);
-  a.fscr = reinterpret_cast<float2*>(base);
-  a.pbuf = reinterpret_cast<float2*>(base + fscr_bytes);
-  int T = 0, min_ch_tail = 1 << 30;
-  // one column-preparation launch for the batch, one row-preparation launch per Z element type
-  PrepColsArgs pc;
-  std::memset(&pc, 0, sizeof(pc));
-  pc.g = g;
-  pc.d_err = d_err;
-  PrepRowsArgs pr[2];  // [0]: complex128 Z, [1]: complex64
-  std::memset(pr, 0, sizeof(pr));
-  pr[0].TJ = pr[1].TJ = TJ;
-  int nr[2] = {0, 0}, max_it[2] = {0, 0}, max_chr[2] = {0, 0}, max_ch = 0;
-  for (int b = 0; b < nb; ++b) {
-    const Plan& P = pl[b];
-    const MixedBlock& B = in[b];
-    BlockDesc& d = a.blk[b];
-    if (B.rows_i > 0 && (B.col0 % TJ != 0 || B.col0 < B.rows_i || B.col0 >= B.n_pb)) return QSGW_ERR_ARG;
-    qsgw_status st = tile_list(s, B.n_pb, B.n_pad, TJ, B.rows_i, B.col0, &d.tiles, &d.n_tiles);
-    if (st != QSGW_OK) return st;
-    d.aplanes = base + P.o_a;
-    d.braw = reinterpret_cast<float2*>(base + P.o_raw);
-    d.wst = reinterpret_cast<float*>(base + P.o_w);
-    d.zmax = reinterpret_cast<float*>(base + P.o_zmax);
-    d.expA = reinterpret_cast<int*>(base + P.o_exp);
-    d.wmax = reinterpret_cast<float*>(base + P.o_wmax);
-    d.acc = reinterpret_cast<float2*>(B.acc);
-    d.acc2 = reinterpret_cast<double*>(d.acc + (size_t)L * 2 * B.n_pad * B.n_pad);
-    d.tile_off = T;
-    d.n_pb = B.n_pb;
-    d.n_pad = B.n_pad;
-    d.n_kb = P.n_kb;
-    d.n_kbr = (int)((P.K + KBR - 1) / KBR);
-    d.n_ch = P.n_ch;
-    T += d.n_tiles;
-    pc.b[b] = PrepColsBlk{B.eo, B.eu, B.wv, reinterpret_cast<float*>(base + P.o_w),
-                          reinterpret_cast<float*>(base + P.o_wmax), P.K, B.n_unocc, P.n_ch};
-    const int t = B.z32 ? 1 : 0;
-    pr[t].b[nr[t]++] = PrepRowsBlk{B.Z, B.ldz, P.K, base + P.o_a, reinterpret_cast<float2*>(base + P.o_raw),
-                                   reinterpret_cast<float*>(base + P.o_zmax), reinterpret_cast<int*>(base + P.o_exp),
-                                   B.n_pb, B.n_pad, P.n_kb, P.n_jt, P.n_ch, P.n_it,
-                                   B.rows_i > 0 ? B.rows_i : B.n_pad, B.rows_i > 0 ? B.col0 : 0};
-    max_ch = std::max(max_ch, P.n_ch);
-    max_chr[t] = std::max(max_chr[t], P.n_ch);
-    max_it[t] = std::max(max_it[t], P.n_it);
-  }
-  prep_cols_kernel<<<dim3(max_ch, nb), PC_THREADS, 0, stream>>>(pc);
-  if (nr[0] > 0) prep_rows_kernel<double2><<<dim3(max_chr[0], max_it[0], nr[0]), 256, 0, stream>>>(pr[0]);
-  if (nr[1] > 0) prep_rows_kernel<float2><<<dim3(max_chr[1], max_it[1], nr[1]), 256, 0, stream>>>(pr[1]);
-  // whole tiles first; the last R tiles (a partial last wave) are split into P chunk ranges
-  const int G = s.n_sm;
-  const int R = T >= G ? T % G : T;
-  a.T = T;
-  a.T_whole = T - R;
-  for (int b = 0; b < nb; ++b) {  // smallest chunk count among blocks that own tail tiles
-    const BlockDesc& d = a.blk[b];
-    if (d.tile_off + d.n_tiles > a.T_whole && d.n_ch < min_ch_tail) min_ch_tail = d.n_ch;
-  }
-  int P = R > 0 ? G / R : 1;
-  if (P < 1) P = 1;
-  if (plan.pieces > 0) P = plan.pieces;
-  if (R > 0 && P > min_ch_tail) P = min_ch_tail;
-  a.P = P;
-  a.n_items = a.T_whole + R * P;
   if (!s.counter && cudaMalloc(&s.counter, sizeof(int)) != cudaSuccess) return QSGW_ERR_NOMEM;
-  a.counter = s.counter;
-  if (cudaMemsetAsync(s.counter, 0, sizeof(int), stream) != cudaSuccess) return QSGW_ERR_CUDA;
-  const int grid = a.n_items < G ? a.n_items : G;
-  herk_mixed_kernel<<<grid, NTHREADS, main_smem_bytes(N, TJ, L), stream>>>(a);
-  if (R > 0) piece_reduce_kernel<<<dim3(R, (N * 128 + 255) / 256), 256, 0, stream>>>(a);
-  return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
+  uint8_t* base = static_cast<uint8_t*>(s.planes);
+  float2* fscr = reinterpret_cast<float2*>(base);
+  float2* pbuf = reinterpret_cast<float2*>(base + fscr_bytes);
+  for (int c0 = 0; c0 < max_ch; c0 += cpl) {
+    MixedBlock sub[kMaxBlocks];
+    long long r0[kMaxBlocks];
+    Geom G[kMaxBlocks];
+    Carve S[kMaxBlocks];
+    const int2* st_tiles[kMaxBlocks];
+    int st_n[kMaxBlocks];
+    int ns = 0;
+    size_t off = 2 * fscr_bytes;
+    for (int b = 0; b < nb; ++b) {
+      const long long c0r = (long long)c0 * CHR;
+      if (Kb[b] <= c0r) continue;  // this block's columns ended in an earlier launch
+      sub[ns] = in[b];
+      sub[ns].Z = advance_cols(in[b].Z, in[b].z32, in[b].ldz, c0r);
+      r0[ns] = c0r;
+      G[ns] = geom_of(in[b].n_pb, in[b].n_pad, std::min(Kb[b] - c0r, (long long)cpl * CHR), TJ);
+      S[ns] = carve(base + off, G[ns], in[b].n_pad, N, L);
+      off += geom_bytes(G[ns], in[b].n_pad, N, L);
+      st_tiles[ns] = tiles[b];
+      st_n[ns] = n_tiles[b];
+      ++ns;
+    }
+    qsgw_status st = launch_blocks(ns, sub, r0, G, S, st_tiles, st_n, g, TJ, plan.pieces, s.n_sm, fscr, pbuf,
+                                   s.counter, d_err, stream);
+    if (st != QSGW_OK) return st;
+  }
+  return QSGW_OK;
 }
 
 qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long ldz, int n_pb, int n_pad, int n_occ,
@@ -1083,22 +1160,24 @@ qsgw_status mixed_accumulate(MixedScratch& s, const void* Z, bool z32, long long
 // ------------------------------------------------------------------ allocation-free variant
 // One block of columns, chi0 written straight to the caller's buffer, every intermediate in a
 // fixed file-scope device array instead of cudaMalloc'd scratch. See qsgw_chi0_block_noalloc.
-constexpr size_t kNoAllocBytes = 64ull << 20;
+// The columns go through the array one chunk of 1024 at a time, so the number of columns does not
+// count against it.
+constexpr size_t kNoAllocBytes = 128ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Upper-triangle tile list of one (n_pb, TJ), in the order tile_list() uses, built on the device.
 __global__ void noalloc_tiles_kernel(int n_pb, int n_it, int n_jt, int TJ, int2* out) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   int k = 0;
-  for (int it = 0; it < n_it; ++it)
-    for (int jt = 0; jt < n_jt; ++jt)
+  for (int jt = 0; jt < n_jt; ++jt)
+    for (int it = 0; it < n_it; ++it)
       if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) out[k++] = make_int2(it, jt);
 }
 
 qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_occ, int n_unocc, const double* eo,
                                const double* eu, const OmegaGrid& g, double spin, double2* chi0, cudaStream_t stream) {
   const int L = g.L, TJ = tile_width(L), N = TJ * L;
-  if (TJ < 1 || N < 16 || N > 256) return QSGW_ERR_ARG;
+  if (TJ < 1) return QSGW_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QSGW_ERR_CUDA;
   // Set-up on every call, in the current context: the array's device address (a lookup, no
@@ -1111,33 +1190,23 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QSGW_ERR_CUDA;
   const int n_pad = pad_to(n_pb, kPad);
   const long long K = (long long)n_occ * n_unocc;
-  const int n_ch = (int)((K + CHR - 1) / CHR), n_kb = n_ch * KB_PER_CH;
+  const int n_ch = (int)((K + CHR - 1) / CHR);
   const int n_it = n_pad / TI, n_jt = (n_pb + TJ - 1) / TJ;
   int n_tiles = 0;
   for (int it = 0; it < n_it; ++it)
     for (int jt = 0; jt < n_jt; ++jt)
       if (jt * TJ + TJ - 1 >= it * TI && it * TI < n_pb) ++n_tiles;
-  // layout inside the fixed array
-  size_t off = 256;  // [0, 256): error flag, work counter
+  // layout inside the fixed array: error flag and work counter, accumulators, tile list, the planes
+  // of one chunk, then per-CTA flush scratch and as many piece partial buffers; the grid is capped to
+  // the CTAs there is room for
+  size_t off = 256;
   const size_t o_acc = off;
   const size_t acc_bytes = (size_t)L * 2 * n_pad * n_pad * (sizeof(float2) + sizeof(double));
   off += align256(acc_bytes);
   const size_t o_tiles = off;
   off += align256((size_t)n_tiles * sizeof(int2));
-  const size_t o_a = off;
-  off += align256((size_t)n_it * n_kb * A_STAGE);
-  const size_t o_raw = off;
-  off += align256((size_t)n_jt * n_kb * KBR * TJ * sizeof(float2));
-  const size_t o_w = off;
-  off += align256((size_t)n_kb * KBR * L * sizeof(float));
-  const size_t o_zmax = off;
-  off += align256((size_t)n_ch * n_pad * sizeof(float));
-  const size_t o_exp = off;
-  off += align256((size_t)n_ch * n_pad * sizeof(int));
-  const size_t o_wmax = off;
-  off += align256((size_t)n_ch * L * sizeof(float));
-  // the rest holds the per-CTA flush scratch and as many piece partial buffers; the grid is capped
-  // to the CTAs there is room for
+  const size_t o_blk = off;
+  off += geom_bytes(geom_of(n_pb, n_pad, std::min(K, (long long)CHR), TJ), n_pad, N, L);
   const size_t o_fscr = off, fscr_cta = (size_t)kFscrPerCta * sizeof(float2);
   if (off + 2 * fscr_cta > kNoAllocBytes) return QSGW_ERR_ARG;  // beyond the fixed array: use the context API
   const int cap_ctas = (int)((kNoAllocBytes - off) / (2 * fscr_cta));
@@ -1149,63 +1218,22 @@ qsgw_status mixed_chi0_noalloc(const double2* Z, long long ldz, int n_pb, int n_
   if (cudaMemsetAsync(base + o_acc, 0, acc_bytes, stream) != cudaSuccess) return QSGW_ERR_CUDA;
   int2* tiles = reinterpret_cast<int2*>(base + o_tiles);
   noalloc_tiles_kernel<<<1, 1, 0, stream>>>(n_pb, n_it, n_jt, TJ, tiles);
-
-  MainArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.nb = 1;
-  a.L = L;
-  a.TJ = TJ;
-  a.N = N;
-  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
-  a.d_err = d_err;
-  BlockDesc& d = a.blk[0];
-  d.aplanes = base + o_a;
-  d.braw = reinterpret_cast<float2*>(base + o_raw);
-  d.wst = reinterpret_cast<float*>(base + o_w);
-  d.zmax = reinterpret_cast<float*>(base + o_zmax);
-  d.expA = reinterpret_cast<int*>(base + o_exp);
-  d.wmax = reinterpret_cast<float*>(base + o_wmax);
-  d.tiles = tiles;
-  d.acc = reinterpret_cast<float2*>(base + o_acc);
-  d.acc2 = reinterpret_cast<double*>(d.acc + (size_t)L * 2 * n_pad * n_pad);
-  d.tile_off = 0;
-  d.n_pb = n_pb;
-  d.n_pad = n_pad;
-  d.n_kb = n_kb;
-  d.n_kbr = (int)((K + KBR - 1) / KBR);
-  d.n_tiles = n_tiles;
-  d.n_ch = n_ch;
-  PrepColsArgs pc;
-  std::memset(&pc, 0, sizeof(pc));
-  pc.g = g;
-  pc.d_err = d_err;
-  pc.b[0] = PrepColsBlk{eo, eu, nullptr, reinterpret_cast<float*>(base + o_w), reinterpret_cast<float*>(base + o_wmax),
-                        K, n_unocc, n_ch};
-  prep_cols_kernel<<<dim3(n_ch, 1), PC_THREADS, 0, stream>>>(pc);
-  PrepRowsArgs pr;
-  std::memset(&pr, 0, sizeof(pr));
-  pr.TJ = TJ;
-  pr.b[0] = PrepRowsBlk{Z, ldz, K, base + o_a, reinterpret_cast<float2*>(base + o_raw),
-                        reinterpret_cast<float*>(base + o_zmax), reinterpret_cast<int*>(base + o_exp),
-                        n_pb, n_pad, n_kb, n_jt, n_ch, n_it, n_pad, 0};
-  prep_rows_kernel<double2><<<dim3(n_ch, n_it, 1), 256, 0, stream>>>(pr);
-  a.fscr = reinterpret_cast<float2*>(base + o_fscr);
-  a.pbuf = reinterpret_cast<float2*>(base + o_fscr + (size_t)cap_ctas * fscr_cta);
-  const int G = n_sm < cap_ctas ? n_sm : cap_ctas, T = n_tiles;
-  const int R = T >= G ? T % G : T;
-  a.T = T;
-  a.T_whole = T - R;
-  int P = R > 0 ? G / R : 1;
-  if (P < 1) P = 1;
-  if (R > 0 && P > n_ch) P = n_ch;
-  a.P = P;
-  a.n_items = a.T_whole + R * P;
-  a.counter = counter;
-  const int grid = a.n_items < G ? a.n_items : G;
-  herk_mixed_kernel<<<grid, NTHREADS, main_smem_bytes(N, TJ, L), stream>>>(a);
-  if (R > 0) piece_reduce_kernel<<<dim3(R, (N * 128 + 255) / 256), 256, 0, stream>>>(a);
+  float2* fscr = reinterpret_cast<float2*>(base + o_fscr);
+  float2* pbuf = reinterpret_cast<float2*>(base + o_fscr + (size_t)cap_ctas * fscr_cta);
+  const int grid_cap = n_sm < cap_ctas ? n_sm : cap_ctas;
+  const int2* tl = tiles;
+  for (int c = 0; c < n_ch; ++c) {
+    const long long r0 = (long long)c * CHR;
+    const Geom G = geom_of(n_pb, n_pad, std::min(K - r0, (long long)CHR), TJ);
+    const Carve S = carve(base + o_blk, G, n_pad, N, L);
+    MixedBlock B{advance_cols(Z, false, ldz, r0), ldz, n_pb, n_pad, n_occ, n_unocc, eo, eu,
+                 reinterpret_cast<float4*>(base + o_acc), false, nullptr};
+    const qsgw_status st =
+        launch_blocks(1, &B, &r0, &G, &S, &tl, &n_tiles, g, TJ, 0, grid_cap, fscr, pbuf, counter, d_err, stream);
+    if (st != QSGW_OK) return st;
+  }
+  launch_finalize_chi(base + o_acc, ACC_DF32, n_pb, n_pad, L, spin, chi0, stream);
   if (cudaGetLastError() != cudaSuccess) return QSGW_ERR_CUDA;
-  launch_finalize_chi(d.acc, ACC_DF32, n_pb, n_pad, L, spin, chi0, stream);
   int h_err = 0;
   if (cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess)
