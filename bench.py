@@ -134,7 +134,7 @@ def run_ours(args, rank, world, dev_index):
     dev = torch.device("cuda", dev_index)
     stream = torch.cuda.Stream(dev)
     gen_q = rank  # weak scaling: every rank assembles its own q-point
-    prec = N.QSGW_MIXED_BF16X3 if args.prec == "mixed" else N.QSGW_FP64
+    prec = N.QSGW_MIXED_F16X3 if args.prec == "mixed" else N.QSGW_FP64
 
     # inputs resident in HBM (generated on the device, untimed). The mixed path holds Z as
     # complex64: it rounds every element to FP32 before forming digits, so this is bit-identical
@@ -142,7 +142,7 @@ def run_ours(args, rank, world, dev_index):
     # the mixed run) uses complex128.
     ncol = N_OCC * N_UNOCC
     nk = args.k_points
-    mixed = prec == N.QSGW_MIXED_BF16X3
+    mixed = prec == N.QSGW_MIXED_F16X3
     Z = torch.empty((nk, ncol, N_PB), dtype=torch.complex64 if mixed else torch.complex128, device=dev)
     eo = torch.from_numpy(np.stack([eps_occ(WL.seed, gen_q, k, N_OCC) for k in range(N_K)])).to(dev)
     eu = torch.from_numpy(np.stack([eps_unocc(WL.seed, gen_q, k, N_UNOCC) for k in range(N_K)])).to(dev)
@@ -289,7 +289,7 @@ def run_batched(args, steps=None, warmup=None):
     npb = [B.n_pb(q) for q in range(B.n_q)]
     nu = [[B.n_unocc(q, k) for k in range(B.n_k)] for q in range(B.n_q)]
     flops = B.flops()
-    ctx = N.qsgw_chi0_init(npb, B.omega, B.spin, N.QSGW_MIXED_BF16X3, stream=stream)
+    ctx = N.qsgw_chi0_init(npb, B.omega, B.spin, N.QSGW_MIXED_F16X3, stream=stream)
     Zq = [torch.empty((B.n_occ * 600, npb[q]), dtype=torch.complex128, device=dev) for q in range(B.n_q)]
     eo = [[torch.from_numpy(eps_occ(B.seed, q, k, B.n_occ)).to(dev) for k in range(B.n_k)] for q in range(B.n_q)]
     eu = [[torch.from_numpy(eps_unocc(B.seed, q, k, nu[q][k])).to(dev) for k in range(B.n_k)] for q in range(B.n_q)]
@@ -372,7 +372,7 @@ def run_large(args):
     n, Lg, no, nu = G.n_pb(0), G.n_omega, G.n_occ, G.n_unocc_fixed
     k_cols = G.n_k * no * nu
     flops = 4.0 * k_cols * n * (n + 1) * Lg
-    ctx = N.qsgw_chi0_init([n], G.omega, G.spin, N.QSGW_MIXED_BF16X3, stream=stream)
+    ctx = N.qsgw_chi0_init([n], G.omega, G.spin, N.QSGW_MIXED_F16X3, stream=stream)
     eo = torch.from_numpy(np.concatenate([eps_occ(G.seed, 0, k, no) for k in range(G.n_k)])).to(dev)
     eu = torch.from_numpy(np.concatenate([eps_unocc(G.seed, 0, k, nu) for k in range(G.n_k)])).to(dev)
     v = torch.from_numpy(coulomb_v(G.seed, 0, n)).to(dev)
@@ -431,7 +431,7 @@ def run_sigx(args):
             Z[k].copy_(tmp)
     torch.cuda.synchronize(dev)
     out = torch.empty((n_qp, n_qp), dtype=torch.complex128, device=dev)
-    ctx = N.qsgw_sigx_init([n_qp], N.QSGW_MIXED_BF16X3, stream=stream)
+    ctx = N.qsgw_sigx_init([n_qp], N.QSGW_MIXED_F16X3, stream=stream)
 
     def step():
         N.qsgw_chi0_reset(ctx, 0)
@@ -504,7 +504,7 @@ def run_realaxis(args):
     S = torch.empty((nb, N_PB, N_PB), dtype=torch.complex128, device=dev)
     bins_out = list(range(20, nb, 12))[:12]
     P = torch.empty((len(bins_out), N_PB, N_PB), dtype=torch.complex128, device=dev)
-    ctx = N.qsgw_spectral_init(N_PB, edges, N.QSGW_MIXED_BF16X3, stream=stream)
+    ctx = N.qsgw_spectral_init(N_PB, edges, N.QSGW_MIXED_F16X3, stream=stream)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def step(record):
@@ -571,7 +571,7 @@ def run_sigc(args):
     n_qp, n_band, n_k = 64, 256, min(16, args.k_points)
     om = np.asarray(WL.omega, dtype=np.float64)
     # W^c from chi0 -> eps^-1 -> W^c (set-up, not timed)
-    ctxc = N.qsgw_chi0_init([N_PB], om, WL.spin, N.QSGW_MIXED_BF16X3, stream=stream)
+    ctxc = N.qsgw_chi0_init([N_PB], om, WL.spin, N.QSGW_MIXED_F16X3, stream=stream)
     tmp = torch.empty((N_OCC * N_UNOCC, N_PB), dtype=torch.complex128, device=dev)
     for k in range(N_K):
         eo = torch.from_numpy(eps_occ(WL.seed, 0, k, N_OCC)).to(dev)
@@ -596,7 +596,7 @@ def run_sigc(args):
             N.qsgw_synth_z(WL.seed, 5, k, N_PB, n_band, n_qp, WL.s_div, Zs[k], N_PB, stream=stream)
     torch.cuda.synchronize(dev)
     out = torch.empty((n_qp, n_qp), dtype=torch.complex128, device=dev)
-    ctx = N.qsgw_sigc_init(n_qp, N_PB, om, N.QSGW_MIXED_BF16X3, stream=stream)
+    ctx = N.qsgw_sigc_init(n_qp, N_PB, om, N.QSGW_MIXED_F16X3, stream=stream)
 
     def step(nk, c, nb=n_band):
         N.qsgw_chi0_reset(c, 0)
@@ -792,7 +792,7 @@ def main():
         roof["tensor_pipe_frac"] = roof["tensor_pipe_issued_tflops"] / sustained
     out = {"metric": metric_name(), "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "bf16x3-exact-digit" if args.prec == "mixed" else "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f16x3-exact-digit" if args.prec == "mixed" else "f64", "data": "synthetic",
            "config": config(args), "roofline": roof, "gpu_launches": res["launches"], "clocks": res["clocks"],
            "e2e": res["e2e"]}
     if res["fp64"]:
@@ -826,7 +826,7 @@ def issued_mma_flops(n_pb, n_omega, k_cols, TJ=None):
     n_it, n_jt = n_pad // 64, (n_pb + TJ - 1) // TJ
     tiles = sum(1 for it in range(n_it) for jt in range(n_jt) if jt * TJ + TJ - 1 >= it * 64 and it * 64 < n_pb)
     n_kb = (k_cols + 15) // 16  # 16-column K-blocks (the last chunk stops at the last column)
-    return tiles * n_kb * 2 * 8 * (2.0 * 128 * n * 16)
+    return tiles * n_kb * 2 * 6 * (2.0 * 128 * n * 16)  # 2 K-steps x 6 digit products per K-block
 
 
 def issued_mma_flops_per_call():

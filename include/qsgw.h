@@ -65,13 +65,15 @@ typedef enum {
 
 typedef enum {
   QSGW_FP64 = 0,        /* FP64 arithmetic end to end (CUDA-core DFMA) */
-  QSGW_MIXED_BF16X3 = 1, /* tcgen05 tensor cores on exact 3-digit BF16 slices, FP32 per chunk,
-                           double-float (2 x FP32) across chunks; eps and W stay FP64 */
+  QSGW_MIXED_F16X3 = 1, /* tcgen05 tensor cores on exact 3-digit slices (an integer leading digit
+                           and two FP16 digits; 6 products per flop pair), FP32 per chunk of 1024
+                           columns, double-float (2 x FP32) across chunks; eps and W stay FP64 */
+  QSGW_MIXED_BF16X3 = 1, /* the same value under its earlier name (the slices were BF16 then) */
   QSGW_MIXED_TF32X3 = 2  /* reserved, rejected by qsgw_chi0_init with QSGW_ERR_ARG: TF32 hi/lo
                             splitting (3 products) has no exact leading level, and the tensor
                             cores' truncating FP32 accumulation leaves 4e-6..1.7e-5 relative error,
                             above the 1e-6 bar; an exact-digit TF32 form needs 6 products at half
-                            the BF16 rate, slower than QSGW_MIXED_BF16X3 */
+                            the FP16 rate, slower than QSGW_MIXED_F16X3 */
 } qsgw_prec;
 
 /* Create a context for n_q independent q-points (Alg. 1 loops over q; each q has its own
@@ -108,7 +110,7 @@ qsgw_status qsgw_chi0_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long 
                                  const double *eps_occ, const double *eps_unocc, int n_omega, const double *omega);
 
 /* Same as qsgw_chi0_accumulate with Z in complex64 (interleaved FP32 re, im; same layout, ldz
- * in elements), for QSGW_MIXED_BF16X3 contexts only (QSGW_ERR_ARG otherwise). The mixed path
+ * in elements), for QSGW_MIXED_F16X3 contexts only (QSGW_ERR_ARG otherwise). The mixed path
  * rounds every element of Z to FP32 before it forms digits, so the result is bit-identical to
  * qsgw_chi0_accumulate on the complex128 data that rounds to this Z. It moves half the bytes
  * (host staging and HBM reads). The paper's mixed precision likewise holds Z in single
@@ -130,7 +132,7 @@ typedef struct {
 
 /* Batched form of qsgw_chi0_accumulate over independent q-points (Alg. 1 loops over q). The
  * blocks must name distinct q (QSGW_ERR_ARG otherwise), at most 32 per call, all pointers on the
- * device. In QSGW_MIXED_BF16X3 every block's operands are prepared and then ONE persistent
+ * device. In QSGW_MIXED_F16X3 every block's operands are prepared and then ONE persistent
  * tensor-core launch works through all (block, tile, chunk) items, balanced over the SMs, so
  * uneven n_pb and column counts share the GPU; in QSGW_FP64 ONE launch of the FP64 kernel covers
  * all (block, tile, K-slice) items, each block cut into the slices the one-block call would use,
@@ -162,7 +164,7 @@ int qsgw_tile_plan_candidates(int n_omega, qsgw_tile_plan *out, int max_out);
  * columns), and later mixed accumulate calls of that class use it. When the environment variable
  * QSGW_TUNE_CACHE names a file, the choice is appended to it, and qsgw_chi0_init of a mixed
  * context reads the plans back from it. chosen and ms_chosen (nullable) receive the plan and its
- * time per launch. QSGW_MIXED_BF16X3 chi0 contexts only (QSGW_ERR_STATE otherwise); QSGW_ERR_NOMEM
+ * time per launch. QSGW_MIXED_F16X3 chi0 contexts only (QSGW_ERR_STATE otherwise); QSGW_ERR_NOMEM
  * if the scratch accumulators do not fit. Synchronises the stream. */
 qsgw_status qsgw_chi0_autotune(qsgw_ctx *ctx, int n_blocks, const qsgw_block *blocks, int reps,
                                qsgw_tile_plan *chosen, float *ms_chosen);
@@ -212,7 +214,7 @@ const char *qsgw_status_string(qsgw_status s);
  * The same tensor-core (or FP64) kernels compute it.
  *
  * Create a context for n_q independent q-points with n_qp[q] states each (1 <= n_qp <= 16384);
- * prec as for qsgw_chi0_init (QSGW_MIXED_BF16X3: <= 1e-6 relative error). qsgw_chi0_finalize
+ * prec as for qsgw_chi0_init (QSGW_MIXED_F16X3: <= 1e-6 relative error). qsgw_chi0_finalize
  * then writes Sigma^x (device complex128 [n_qp][n_qp], column-major, full Hermitian, negative
  * semidefinite); qsgw_chi0_reset / sync / destroy apply. The chi0-only calls
  * (qsgw_chi0_accumulate*, qsgw_eps_inv, qsgw_chi0_accumulate_batch / _synthetic) return
@@ -228,7 +230,7 @@ qsgw_status qsgw_sigx_init(qsgw_ctx **ctx, int n_q, const int *n_qp, qsgw_prec p
  * Host arrays follow the same rules as in qsgw_chi0_accumulate. */
 qsgw_status qsgw_sigx_accumulate(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_pb,
                                  const double *v);
-/* Same with Z in complex64 (QSGW_MIXED_BF16X3 contexts only; bit-identical to complex128 input
+/* Same with Z in complex64 (QSGW_MIXED_F16X3 contexts only; bit-identical to complex128 input
  * that rounds to this Z, as for qsgw_chi0_accumulate_c64). */
 qsgw_status qsgw_sigx_accumulate_c64(qsgw_ctx *ctx, int q, const void *Z, long long ldz, int n_occ, int n_pb,
                                      const double *v);
@@ -331,7 +333,7 @@ qsgw_status qsgw_selftest_wait_timeout(double limit_seconds, void *cuda_stream);
  * chi0 of ONE block of transition columns, computed in mixed precision exactly as
  * qsgw_chi0_accumulate + qsgw_chi0_finalize would on a fresh context, but without allocating
  * any device memory: every intermediate (digit planes, weights, tile list, accumulators, error
- * flag) lives in one fixed 64 MiB array in the library's device image. It is for callers that
+ * flag) lives in one fixed 128 MiB array in the library's device image. It is for callers that
  * cannot call cudaMalloc: code whose device memory is entirely reserved by another allocator
  * (a framework's caching pool or a fixed arena), code that must not risk the implicit device
  * synchronisation cudaMalloc/cudaFree may cause, and code paths that are not allowed to fail on
@@ -344,9 +346,11 @@ qsgw_status qsgw_selftest_wait_timeout(double limit_seconds, void *cuda_stream);
  *   cuda_stream            stream the work is ordered on; the call synchronises it at the end to
  *                          return device-detected errors (QSGW_ERR_DOMAIN, QSGW_ERR_TIMEOUT)
  * Sizes whose intermediates do not fit the fixed array return QSGW_ERR_ARG (use the context
- * API instead); n_pb <= 256 with n_occ * n_unocc <= 3072 always fits. The space left after the
- * accumulators and operands holds one flush area per CTA, and the tensor-core grid is capped at
- * the CTAs it has room for (about 15 at that corner, more for smaller blocks). Every call looks
+ * API instead). The columns go through the array one chunk of 1024 at a time, so their number
+ * does not count: n_pb <= 256 always fits, with any n_occ * n_unocc. The space left after the
+ * accumulators and one chunk's digit planes holds one flush area per CTA, and the tensor-core grid
+ * is capped at the CTAs it has room for (about 80 at n_pb = 256 with 16 frequencies, the SM count for
+ * smaller blocks). Every call looks
  * up the array's device address in the current context (and sets the kernel's shared-memory
  * limit there), so the call stays valid after the context is reset. All calls share the one
  * array: calls whose GPU work overlaps (other streams, other host threads) race and must not be

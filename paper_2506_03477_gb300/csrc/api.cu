@@ -221,7 +221,7 @@ qsgw_status qsgw_chi0_init(qsgw_ctx** out, int n_q, const int* n_pb, int n_omega
   *out = nullptr;
   if (n_q < 1 || !n_pb || n_omega < 1 || n_omega > kMaxOmega || !omega || !std::isfinite(spin_factor))
     return QSGW_ERR_ARG;
-  if (prec != QSGW_FP64 && prec != QSGW_MIXED_BF16X3) return QSGW_ERR_ARG;
+  if (prec != QSGW_FP64 && prec != QSGW_MIXED_F16X3) return QSGW_ERR_ARG;
   for (int i = 0; i < n_q; ++i)
     if (n_pb[i] < 1 || n_pb[i] > kMaxNpb) return QSGW_ERR_ARG;
   for (int l = 0; l < n_omega; ++l)
@@ -260,7 +260,7 @@ qsgw_status qsgw_chi0_init(qsgw_ctx** out, int n_q, const int* n_pb, int n_omega
     qsgw_chi0_destroy(c);
     return st;
   }
-  if (prec == QSGW_MIXED_BF16X3) load_plans(c);
+  if (prec == QSGW_MIXED_F16X3) load_plans(c);
   *out = c;
   return QSGW_OK;
 }
@@ -275,7 +275,7 @@ qsgw_status accumulate_any(qsgw_ctx* c, int q, const void* Z, bool z32, long lon
                            const double* eps_occ, const double* eps_unocc, int n_omega, const double* omega) {
   const bool sx = c && c->sigx;
   if (!c || q < 0 || q >= c->n_q || !Z || (!sx && !eps_occ) || !eps_unocc) return QSGW_ERR_ARG;
-  if (z32 && c->prec != QSGW_MIXED_BF16X3) return QSGW_ERR_ARG;
+  if (z32 && c->prec != QSGW_MIXED_F16X3) return QSGW_ERR_ARG;
   const QAcc& a = c->q[q];
   if (ldz < a.n_pb || n_occ < 1 || n_unocc < 1) return QSGW_ERR_ARG;
   if ((long long)n_occ * n_unocc > (1LL << 31)) return QSGW_ERR_ARG;
@@ -584,7 +584,7 @@ int qsgw_tile_plan_candidates(int n_omega, qsgw_tile_plan* out, int max_out) {
 
 qsgw_status qsgw_chi0_set_tile_plan(qsgw_ctx* c, const qsgw_tile_plan* plan) {
   if (!c) return QSGW_ERR_ARG;
-  if (c->prec != QSGW_MIXED_BF16X3) return QSGW_ERR_STATE;
+  if (c->prec != QSGW_MIXED_F16X3) return QSGW_ERR_STATE;
   if (!plan) {
     c->mixed.use_forced = false;
     return QSGW_OK;
@@ -601,7 +601,7 @@ qsgw_status qsgw_chi0_autotune(qsgw_ctx* c, int n_blocks, const qsgw_block* bloc
   MixedBlock mb[32];
   qsgw_status st = batch_blocks(c, n_blocks, blocks, mb);
   if (st != QSGW_OK) return st;
-  if (c->prec != QSGW_MIXED_BF16X3) return QSGW_ERR_STATE;
+  if (c->prec != QSGW_MIXED_F16X3) return QSGW_ERR_STATE;
   if (reps < 1 || reps > 100) return QSGW_ERR_ARG;
   TilePlan best;
   float ms = 0.f;
@@ -868,7 +868,7 @@ qsgw_status qsgw_sigc_init(qsgw_ctx** ctx, int n_qp, int n_pb, int n_omega, cons
     return QSGW_ERR_ARG;
   for (int i = 0; i < n_omega; ++i)
     if (!std::isfinite(omega[i]) || !(omega[i] > 0.0) || (i > 0 && !(omega[i] > omega[i - 1]))) return QSGW_ERR_ARG;
-  if (prec == QSGW_MIXED_BF16X3 && mixed_tile_cols(1) != kSigcAlign) return QSGW_ERR_ARG;
+  if (prec == QSGW_MIXED_F16X3 && mixed_tile_cols(1) != kSigcAlign) return QSGW_ERR_ARG;
   const int nbb = std::max(1, kSigcRows / n_qp);
   const int Y3 = pad_to(n_qp, kSigcAlign);
   const int npb[2] = {Y3 + n_qp, pad_to(nbb * n_qp, kSigcAlign) + n_pb};

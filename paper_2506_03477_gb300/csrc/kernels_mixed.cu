@@ -14,17 +14,18 @@
 // Exact leading digit. tcgen05 accumulates FP32 with truncation (round toward zero, measured),
 // so a plain float split would drift. Every operand value x of a chunk of 1024 columns is scaled
 // by a power of two 2^e chosen from the chunk maximum (|x 2^e| <= 90) and split as
-//   x 2^e = d0 + d1 + d2 + rem,  d0 = rint(x 2^e) in [-90, 90],  d1 = bf16(x 2^e - d0),
-//   d2 = bf16(x 2^e - d0 - d1),  |rem| <= 2^-19,
-// all three exact BF16 values. Products d0_A d0_B are integers and a chunk sum of them stays
-// below 2 * 1024 * 90^2 < 2^24, so the level-0 TMEM accumulator is exact. The seven products
-// d0 d1, d1 d0, d0 d2, d2 d0, d1 d1, d1 d2, d2 d1 share a second accumulator whose truncation
-// error is relative to its own, ~2^-6 smaller, magnitude. That error is the largest one left
-// and grows faster than linearly with the chunk length (more truncating adds into a larger
-// sum), which is what bounds CHR: 2048-column chunks measured 1.8e-6 relative on a narrow
-// block, above the 1e-6 bar, against ~0.4e-6 at 1024. The dropped d2 d2 term and the
-// remainders are ~2^-23 of a typical product, at the level of the FP32 rounding of the inputs
-// (d1 d2 alone would be ~2^-20 of a typical product, which is why it is kept). After each chunk
+//   x 2^e = d0 + d1 + d2 + rem,  d0 = rint(x 2^e) in [-90, 90],  d1 = fp16(x 2^e - d0),
+//   d2 = fp16(x 2^e - d0 - d1),  |rem| <= 2^-24,
+// all three exact FP16 values (11 significant bits each; d0 is an integer). Products d0_A d0_B are
+// integers and a chunk sum of them stays below 2 * 1024 * 90^2 < 2^24, so the level-0 TMEM
+// accumulator is exact. The five products d0 d1, d1 d0, d0 d2, d2 d0, d1 d1 share a second
+// accumulator whose truncation error is relative to its own, ~2^-6 smaller, magnitude. That error
+// is the largest one left and grows faster than linearly with the chunk length (more truncating
+// adds into a larger sum), which is what bounds CHR: 2048-column chunks measured 1.8e-6 relative
+// on a narrow block, above the 1e-6 bar, against ~0.4e-6 at 1024. With |d1| <= 1/2 and |d2| <=
+// 2^-12 the dropped products d1 d2, d2 d1 and d2 d2 are below 2^-13 each, ~2^-26 of the largest
+// product 90^2, under the FP32 rounding of the inputs; so 6 MMA products serve a flop pair (BF16
+// digits, 8 significant bits, left d1 d2 at ~2^-20 and needed 8). After each chunk
 // both accumulators are stashed, and two drainer warps scale them by 2^-(eA+eB) (exact) and add
 // them into a double-float (2 x FP32) accumulator in global memory while the next chunk's MMAs
 // run; GB300's FP64 rate (~1.2 TFLOP/s) would make an FP64 read-modify-write here the bottleneck.
@@ -37,6 +38,8 @@
 #include <algorithm>
 #include <cstring>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "mixed.cuh"
 #include "tc_ptx.cuh"
@@ -77,47 +80,42 @@ __device__ __forceinline__ float exp2i(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-// Digit arithmetic. The leading digit is rounded on the FP32 pipe (rintf and F2F would use the
-// quarter-rate conversion pipe); the 8-bit splits use two integer operations each, which measured
-// faster than three FP32 ones. The _rn intrinsics are never contracted into FMAs, which the
-// rounding tricks below rely on.
+// Digit arithmetic. The leading digit is rounded on the FP32 pipe by the add-subtract of 1.5 * 2^23;
+// the FP16 digits come from the FP32 -> FP16 conversion (round to nearest even, FP16 subnormals
+// included) and back. The _rn intrinsics are never contracted into FMAs, which the rounding relies on.
 // (t + 1.5*2^23) - 1.5*2^23 is t rounded to the nearest integer (ties to even) for |t| < 2^22.
 __device__ __forceinline__ float rint_add(float t) {
   return __fsub_rn(__fadd_rn(t, 12582912.0f), 12582912.0f);
 }
 
-// Leading 8 significant bits of x, rounded to nearest (ties away from zero), in the integer
-// domain: add half a unit of the 8th bit to the bit pattern (a carry moves into the exponent
-// correctly), then clear the low 16 bits. Two integer operations instead of three FP32 ones.
-__device__ __forceinline__ float hi8_int(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x8000u) & 0xFFFF0000u);
-}
-// Three BF16-exact digits of t (|t| <= DMAX + 1/2): d0 = rint(t) (integer), then the remainder split
-// twice into leading 8-bit parts. t - d0 and u - d1 are exact in FP32 (Sterbenz).
+// The FP16 value nearest to x, as an FP32 value.
+__device__ __forceinline__ float h16(float x) { return __half2float(__float2half_rn(x)); }
+
+// Three FP16-exact digits of t (|t| <= DMAX + 1/2): d0 = rint(t) (integer), then the remainder
+// split twice into FP16 parts. t - d0 and u - d1 are exact in FP32 (d1 is within a factor of two
+// of u, or u is below the FP16 normal range and u - d1 is a multiple of u's own last bit).
 __device__ __forceinline__ void digits3(float t, float& d0, float& d1, float& d2) {
   d0 = rint_add(t);
   const float u = __fsub_rn(t, d0);
-  d1 = hi8_int(u);
-  const float u2 = __fsub_rn(u, d1);
-  d2 = hi8_int(u2);
+  d1 = h16(u);
+  d2 = h16(__fsub_rn(u, d1));
 }
 
-// Three BF16-exact digits of the exact product a * b (|a b| <= DMAX + 1/2), with the product fused
+// Three FP16-exact digits of the exact product a * b (|a b| <= DMAX + 1/2), with the product fused
 // into the rounding: fma(a, b, 1.5 * 2^23) rounds a b to the nearest integer in one step, and
 // u = fma(a, b, -d0) is a b - d0 rounded once (|u| <= 1/2), so d0 + d1 + d2 follows the exact
-// product rather than fl(a b). Three FP32 operations where a product and digits3 take four.
-// d2 is only ever packed (pack_bf16 keeps the upper 16 bits), so its low half is left uncleared.
+// product rather than fl(a b).
 __device__ __forceinline__ void digits3_mul(float a, float b, float& d0, float& d1, float& d2) {
   d0 = __fsub_rn(__fmaf_rn(a, b, 12582912.0f), 12582912.0f);
   const float u = __fmaf_rn(a, b, -d0);
-  d1 = hi8_int(u);
-  const float u2 = __fsub_rn(u, d1);
-  d2 = __uint_as_float(__float_as_uint(u2) + 0x8000u);  // rounded; low 16 bits dropped by the pack
+  d1 = h16(u);
+  d2 = h16(__fsub_rn(u, d1));
 }
 
-// Two BF16-exact FP32 values -> packed bf16x2 (lo in the low half): their upper 16 bits.
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+// Two FP16-exact FP32 values -> packed f16x2 (lo in the low half); the conversion is exact.
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 // ------------------------------------------------------------------ prep: columns
@@ -304,14 +302,14 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
 #pragma unroll
       for (int pl = 0; pl < 3; ++pl) {
         uint4 re, im;  // Re row: (a, b) pairs; Im row: (-b, a) pairs
-        re.x = pack_bf16(da[pl][0], db[pl][0]);
-        re.y = pack_bf16(da[pl][1], db[pl][1]);
-        re.z = pack_bf16(da[pl][2], db[pl][2]);
-        re.w = pack_bf16(da[pl][3], db[pl][3]);
-        im.x = pack_bf16(-db[pl][0], da[pl][0]);
-        im.y = pack_bf16(-db[pl][1], da[pl][1]);
-        im.z = pack_bf16(-db[pl][2], da[pl][2]);
-        im.w = pack_bf16(-db[pl][3], da[pl][3]);
+        re.x = pack_h2(da[pl][0], db[pl][0]);
+        re.y = pack_h2(da[pl][1], db[pl][1]);
+        re.z = pack_h2(da[pl][2], db[pl][2]);
+        re.w = pack_h2(da[pl][3], db[pl][3]);
+        im.x = pack_h2(-db[pl][0], da[pl][0]);
+        im.y = pack_h2(-db[pl][1], da[pl][1]);
+        im.z = pack_h2(-db[pl][2], da[pl][2]);
+        im.w = pack_h2(-db[pl][3], da[pl][3]);
         const int mre = il, mim = TI + il;
         *reinterpret_cast<uint4*>(base + pl * A_PLANE + (mre >> 3) * 128 + (mre & 7) * 16) = re;
         *reinterpret_cast<uint4*>(base + pl * A_PLANE + (mim >> 3) * 128 + (mim & 7) * 16) = im;
@@ -335,10 +333,10 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
           uint4 v;
-          v.x = pack_bf16(d[pl][0], d[pl][1]);
-          v.y = pack_bf16(d[pl][2], d[pl][3]);
-          v.z = pack_bf16(d[pl][4], d[pl][5]);
-          v.w = pack_bf16(d[pl][6], d[pl][7]);
+          v.x = pack_h2(d[pl][0], d[pl][1]);
+          v.y = pack_h2(d[pl][2], d[pl][3]);
+          v.z = pack_h2(d[pl][4], d[pl][5]);
+          v.w = pack_h2(d[pl][6], d[pl][7]);
           *reinterpret_cast<uint4*>(dst + pl * BPLANE) = v;
         }
       }
@@ -441,7 +439,7 @@ __device__ __forceinline__ void df_add(float2& v, float x) {
   v.y += e;
 }
 
-// Bytes of the B digit planes of one K-block of one J tile (3 planes of N rows x 32 K' BF16).
+// Bytes of the B digit planes of one K-block of one J tile (3 planes of N rows x 32 K' FP16).
 __host__ __device__ constexpr size_t b_stage_bytes(int N) { return (size_t)3 * 64 * N; }
 
 __host__ __device__ constexpr size_t main_smem_bytes(int N) {
@@ -579,14 +577,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             const uint64_t b1 = make_smem_desc(bo + BPLANE, 16 * N, 128, 0);
             const uint64_t b2 = make_smem_desc(bo + 2 * BPLANE, 16 * N, 128, 0);
             const uint32_t acc_in = (kbl == 0 && ks == 0) ? 0u : 1u;
-            mma_bf16(tmem, a0, b0, idesc, acc_in);
-            mma_bf16(tmem + TMEM_L12, a0, b1, idesc, acc_in);
-            mma_bf16(tmem + TMEM_L12, a1, b0, idesc, 1u);
-            mma_bf16(tmem + TMEM_L12, a0, b2, idesc, 1u);
-            mma_bf16(tmem + TMEM_L12, a2, b0, idesc, 1u);
-            mma_bf16(tmem + TMEM_L12, a1, b1, idesc, 1u);
-            mma_bf16(tmem + TMEM_L12, a1, b2, idesc, 1u);
-            mma_bf16(tmem + TMEM_L12, a2, b1, idesc, 1u);
+            mma_f16(tmem, a0, b0, idesc, acc_in);
+            mma_f16(tmem + TMEM_L12, a0, b1, idesc, acc_in);
+            mma_f16(tmem + TMEM_L12, a1, b0, idesc, 1u);
+            mma_f16(tmem + TMEM_L12, a0, b2, idesc, 1u);
+            mma_f16(tmem + TMEM_L12, a2, b0, idesc, 1u);
+            mma_f16(tmem + TMEM_L12, a1, b1, idesc, 1u);
           }
           mma_commit(&empty[s]);
           if (kbl == KB_PER_CH - 1 || kbi == nkb - 1) mma_commit(accfull);  // an item ends a chunk
@@ -977,7 +973,7 @@ static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* 
   a.L = L;
   a.TJ = TJ;
   a.N = N;
-  a.idesc = make_idesc_bf16_f32(128, (uint32_t)N);
+  a.idesc = make_idesc_f16_f32(128, (uint32_t)N);
   a.d_err = d_err;
   a.fscr = fscr;
   a.pbuf = pbuf;

@@ -89,16 +89,16 @@ __device__ __forceinline__ uint64_t make_smem_desc(uint32_t saddr, uint32_t lbo_
   return d;
 }
 
-// Instruction descriptor for kind::f16 with BF16 A/B, FP32 D, both operands K-major.
-// Bits: D format [4,6)=1 (F32); A format [7,10)=1 (BF16); B format [10,13)=1 (BF16);
-// A/B major bits 15/16 = 0 (K-major); N>>3 in [17,23); M>>4 in [24,29).
-__host__ __device__ constexpr uint32_t make_idesc_bf16_f32(uint32_t M, uint32_t N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+// Instruction descriptor for kind::f16 with FP16 A and B (the same type on both sides), FP32 D,
+// both operands K-major. Bits: D format [4,6)=1 (F32); A format [7,10)=0 (F16); B format
+// [10,13)=0 (F16); A/B major bits 15/16 = 0 (K-major); N>>3 in [17,23); M>>4 in [24,29).
+__host__ __device__ constexpr uint32_t make_idesc_f16_f32(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 // ---------------------------------------------------------------- MMA
-// D[tmem] (+)= A[smem] * B[smem]^T, single-CTA, issued by one thread.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+// D[tmem] (+)= A[smem] * B[smem]^T, single-CTA, issued by one thread (operand types in idesc).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"

@@ -23,7 +23,8 @@ QSGW_ERR_NOT_PD = -5
 QSGW_ERR_TIMEOUT = -6
 QSGW_ERR_STATE = -7
 QSGW_FP64 = 0
-QSGW_MIXED_BF16X3 = 1
+QSGW_MIXED_F16X3 = 1
+QSGW_MIXED_BF16X3 = QSGW_MIXED_F16X3  # earlier name of the same mode
 QSGW_MIXED_TF32X3 = 2  # reserved: rejected with QSGW_ERR_ARG
 
 EXPORTS = [

@@ -76,7 +76,7 @@ def test_every_candidate_plan_passes_parity(N, L):
     cands = N.qsgw_tile_plan_candidates(L)
     assert len(cands) == 6
     for plan in cands:
-        ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], omega_grid(L), 2.0, N.QSGW_MIXED_BF16X3)
+        ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], omega_grid(L), 2.0, N.QSGW_MIXED_F16X3)
         try:
             N.qsgw_chi0_set_tile_plan(ctx, plan)
             for k in range(2):
@@ -93,7 +93,7 @@ def test_autotune_leaves_chi0_untouched_and_persists(N, tmp_path, monkeypatch):
     monkeypatch.setenv("QSGW_TUNE_CACHE", str(cache))
     refs = _oracle(L)
     blocks = [_blocks(0), _blocks(1)]
-    ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], omega_grid(L), 2.0, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], omega_grid(L), 2.0, N.QSGW_MIXED_F16X3)
     try:
         N.qsgw_chi0_accumulate_batch(ctx, blocks[0])
         plan, ms = N.qsgw_chi0_autotune(ctx, blocks[1], reps=2)  # between the two accumulate calls
@@ -109,7 +109,7 @@ def test_autotune_leaves_chi0_untouched_and_persists(N, tmp_path, monkeypatch):
     # a new context reads the plan back (a malformed line is skipped) and uses it
     with open(cache, "a") as f:
         f.write("not a plan line\n")
-    ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], omega_grid(L), 2.0, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], omega_grid(L), 2.0, N.QSGW_MIXED_F16X3)
     try:
         for k in range(2):
             N.qsgw_chi0_accumulate_batch(ctx, blocks[k])

@@ -68,8 +68,8 @@ def _oracle(n_k=2):
 
 
 def test_batch_mixed_uneven_q(N):
-    got = _run(N, N.QSGW_MIXED_BF16X3, batched=True)
-    seq = _run(N, N.QSGW_MIXED_BF16X3, batched=False)
+    got = _run(N, N.QSGW_MIXED_F16X3, batched=True)
+    seq = _run(N, N.QSGW_MIXED_F16X3, batched=False)
     for g, s_, r in zip(got, seq, _oracle()):
         for l in range(12):
             assert rel_fro(g[l], r[l]) <= 1e-6
@@ -89,7 +89,7 @@ def test_batch_fp64_equals_sequential(N):
 
 
 def test_batch_argument_errors(N):
-    ctx = N.qsgw_chi0_init([64, 64], OMEGA, 2.0, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([64, 64], OMEGA, 2.0, N.QSGW_MIXED_F16X3)
     try:
         zt, eo, eu = _inputs(0, 0, 64, 2, 3)
         Z, EO, EU = _dev(zt), _dev(eo), _dev(eu)
@@ -109,9 +109,9 @@ def test_batch_argument_errors(N):
 def test_batch_graph_capture_replay(N):
     """After a warm-up call, the batched sequence is only kernel launches: capture it in a CUDA graph
     on the context's stream and replay it; the result equals the directly launched sequence."""
-    ref = _run(N, N.QSGW_MIXED_BF16X3, batched=True)
+    ref = _run(N, N.QSGW_MIXED_F16X3, batched=True)
     stream = torch.cuda.Stream()
-    ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], OMEGA, 2.0, N.QSGW_MIXED_BF16X3, stream=stream)
+    ctx = N.qsgw_chi0_init([s[0] for s in SHAPES], OMEGA, 2.0, N.QSGW_MIXED_F16X3, stream=stream)
     try:
         dev = {}
         for q, (n, no, nu) in enumerate(SHAPES):
@@ -149,7 +149,7 @@ def test_batched_workload_full_size_sampled(N):
     Oracle on the diagonal and a 4x4 block of sampled rows of every q-point."""
     wl = BATCHED
     npb = [wl.n_pb(q) for q in range(wl.n_q)]
-    ctx = N.qsgw_chi0_init(npb, wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init(npb, wl.omega, wl.spin, N.QSGW_MIXED_F16X3)
     got = []
     try:
         eo_d = {}
@@ -193,7 +193,7 @@ def test_batch_many_short_items(N):
     publishes items ahead of the consumers by up to NS + 1; this holds only while the item ring is
     longer than that, which tiles of many K-blocks never tested."""
     shapes = [(600, 1, nu) for nu in (13, 16, 5, 9, 1, 16, 32, 11, 3, 16, 7, 29, 2, 16, 16, 8)]
-    ctx = N.qsgw_chi0_init([s[0] for s in shapes], OMEGA, 2.0, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([s[0] for s in shapes], OMEGA, 2.0, N.QSGW_MIXED_F16X3)
     got = []
     try:
         for k in range(2):

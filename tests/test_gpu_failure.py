@@ -30,5 +30,5 @@ def test_bounded_wait_times_out_and_device_stays_usable(N):
     assert N.qsgw_selftest_wait_timeout(0.05) == N.QSGW_ERR_TIMEOUT
     assert time.perf_counter() - t < 5.0
     assert N.qsgw_selftest_wait_timeout(5.0) == N.QSGW_ERR_ARG  # the limit is bounded
-    chi, Z, d = run_workload(N, TINY, N.QSGW_MIXED_BF16X3)
+    chi, Z, d = run_workload(N, TINY, N.QSGW_MIXED_F16X3)
     assert rel_fro(chi, oracle.chi0_full(Z, d, TINY.omega, TINY.spin)) <= 1e-6

@@ -30,7 +30,7 @@ def N():
     return native
 
 
-@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_BF16X3", 1e-6)])
+@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_F16X3", 1e-6)])
 def test_gpu_output_invariants(N, prec_name, tol):
     wl = Workload("inv", n_q=1, n_k=2, n_occ=8, n_omega=12, s_div=50.0, n_pb_fixed=160, n_unocc_fixed=125, seed=21)
     n, L = 160, 12

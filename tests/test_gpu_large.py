@@ -26,7 +26,7 @@ def N():
 def test_large_streamed_mixed_sampled(N):
     wl = LARGE
     n, L, no, nu = wl.n_pb(0), wl.n_omega, wl.n_occ, wl.n_unocc_fixed
-    ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_F16X3)
     try:
         eo = _dev(np.concatenate([eps_occ(wl.seed, 0, k, no) for k in range(wl.n_k)]))
         eu = _dev(np.concatenate([eps_unocc(wl.seed, 0, k, nu) for k in range(wl.n_k)]))

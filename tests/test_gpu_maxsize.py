@@ -23,7 +23,7 @@ def N():
     return native
 
 
-@pytest.mark.parametrize("prec_name,tol", [("QSGW_MIXED_BF16X3", 1e-6), ("QSGW_FP64", 1e-12)])
+@pytest.mark.parametrize("prec_name,tol", [("QSGW_MIXED_F16X3", 1e-6), ("QSGW_FP64", 1e-12)])
 def test_max_npb_sampled_rows(N, prec_name, tol):
     n, no, nu, om = 16384, 2, 20, np.array([0.01, 0.3])
     zt = z_block(13, 0, 0, n, no, nu, 2000.0)  # (K, n): the column-major n x K matrix

@@ -37,7 +37,7 @@ def _check_chi(chi, ref):
 
 
 def test_tiny_mixed(N):
-    chi, Z, d = run_workload(N, TINY, N.QSGW_MIXED_BF16X3)
+    chi, Z, d = run_workload(N, TINY, N.QSGW_MIXED_F16X3)
     ref = oracle.chi0_full(Z, d, TINY.omega, TINY.spin)
     _check_chi(chi, ref)
 
@@ -49,15 +49,15 @@ def test_tiny_mixed(N):
 def test_ragged_shapes_mixed(N, n_pb, n_occ, n_unocc, L):
     wl = Workload(f"ragged {n_pb}", n_q=1, n_k=2, n_occ=n_occ, n_omega=L, s_div=50.0, n_pb_fixed=n_pb,
                   n_unocc_fixed=n_unocc, seed=11)
-    chi, Z, d = run_workload(N, wl, N.QSGW_MIXED_BF16X3)
+    chi, Z, d = run_workload(N, wl, N.QSGW_MIXED_F16X3)
     ref = oracle.chi0_full(Z, d, wl.omega, wl.spin)
     _check_chi(chi, ref)
 
 
 def test_split_invariance_mixed(N):
     wl = Workload("split", n_q=1, n_k=2, n_occ=12, n_omega=12, s_div=30.0, n_pb_fixed=150, n_unocc_fixed=90, seed=3)
-    a, Z, d = run_workload(N, wl, N.QSGW_MIXED_BF16X3)
-    b, _, _ = run_workload(N, wl, N.QSGW_MIXED_BF16X3, split=5)
+    a, Z, d = run_workload(N, wl, N.QSGW_MIXED_F16X3)
+    b, _, _ = run_workload(N, wl, N.QSGW_MIXED_F16X3, split=5)
     ref = oracle.chi0_full(Z, d, wl.omega, wl.spin)
     _check_chi(a, ref)
     _check_chi(b, ref)
@@ -65,7 +65,7 @@ def test_split_invariance_mixed(N):
 
 def test_domain_error_mixed(N):
     n = 48
-    ctx = N.qsgw_chi0_init([n], [0.01, 0.1], 2.0, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([n], [0.01, 0.1], 2.0, N.QSGW_MIXED_F16X3)
     try:
         zt = z_block(1, 0, 0, n, 2, 3, 16.0)
         N.qsgw_chi0_accumulate(ctx, 0, _dev(zt), n, 2, 3, _dev(np.array([-0.5, 0.2])), _dev(np.array([0.1, 0.3, 0.9])),
@@ -82,11 +82,11 @@ def test_midsize_mixed_chi0_and_w(N):
     """n_pb=256 with four k-points of the medium generator (K=64000, 12 frequencies): full chi0 and W."""
     wl = Workload("mid", n_q=1, n_k=4, n_occ=40, n_omega=12, s_div=200.0, n_pb_fixed=256, n_unocc_fixed=400, seed=1)
     n, L = 256, 12
-    chi, Z, d = run_workload(N, wl, N.QSGW_MIXED_BF16X3)
+    chi, Z, d = run_workload(N, wl, N.QSGW_MIXED_F16X3)
     ref = oracle.chi0_full(Z, d, wl.omega, wl.spin)
     _check_chi(chi, ref)
     v = coulomb_v(wl.seed, 0, n)
-    ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_F16X3)
     try:
         for k in range(wl.n_k):
             zt = z_block(wl.seed, 0, k, n, wl.n_occ, 400, wl.s_div)
@@ -110,7 +110,7 @@ def test_medium_mixed_full_size_sampled(N):
     launch configuration the benchmark times; oracle on a sampled block of entries incl. the diagonal."""
     wl = MEDIUM
     n = wl.n_pb(0)
-    ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_F16X3)
     try:
         Zd = torch.empty((wl.n_occ * 400, n), dtype=torch.complex128, device="cuda")
         for k in range(wl.n_k):
@@ -148,7 +148,7 @@ def test_pinned_host_blocks_double_buffered(N):
         blocks.append((zt, eps_occ(wl.seed, 0, k, no), eps_unocc(wl.seed, 0, k, nu), no, nu))
 
     def run(mode):
-        ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+        ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_F16X3)
         keep = []
         try:
             for zt, eo, eu, no, nu in blocks:
@@ -188,7 +188,7 @@ def test_complex64_input_is_bit_identical(N):
         blocks.append((zt, eps_occ(wl.seed, 0, k, no), eps_unocc(wl.seed, 0, k, nu), no, nu))
 
     def run(mode):
-        ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_BF16X3)
+        ctx = N.qsgw_chi0_init([n], wl.omega, wl.spin, N.QSGW_MIXED_F16X3)
         keep = []
         try:
             for zt, eo, eu, no, nu in blocks:

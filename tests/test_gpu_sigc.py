@@ -85,7 +85,7 @@ def _bound(Zc, e_qp, e_band, Wc):
     return A
 
 
-@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_BF16X3", 2e-6)])
+@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_F16X3", 2e-6)])
 @pytest.mark.parametrize("n_qp,n_pb,bands", [(5, 37, [7, 3]), (700, 70, [12])])
 def test_sigc_against_oracle(N, prec_name, tol, n_qp, n_pb, bands):
     Zc, e_qp, e_band, Wc = _case(31, n_qp, n_pb, bands)
@@ -100,10 +100,10 @@ def test_sigc_against_oracle(N, prec_name, tol, n_qp, n_pb, bands):
 def test_sigc_deterministic_and_reset(N):
     n_qp, n_pb = 9, 40
     Zc, e_qp, e_band, Wc = _case(37, n_qp, n_pb, [6])
-    a = _gpu(N, N.QSGW_MIXED_BF16X3, n_qp, n_pb, Zc, e_qp, e_band, Wc)
-    b = _gpu(N, N.QSGW_MIXED_BF16X3, n_qp, n_pb, Zc, e_qp, e_band, Wc)
+    a = _gpu(N, N.QSGW_MIXED_F16X3, n_qp, n_pb, Zc, e_qp, e_band, Wc)
+    b = _gpu(N, N.QSGW_MIXED_F16X3, n_qp, n_pb, Zc, e_qp, e_band, Wc)
     assert np.array_equal(a, b)
-    ctx = N.qsgw_sigc_init(n_qp, n_pb, OMEGA, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_sigc_init(n_qp, n_pb, OMEGA, N.QSGW_MIXED_F16X3)
     try:
         Z, eb, W, eq = _dev(Zc[0]), _dev(e_band[0]), _dev(np.ascontiguousarray(Wc[0].transpose(0, 2, 1))), _dev(e_qp)
         N.qsgw_sigc_accumulate(ctx, Z, n_pb, 6, eq, eb, W)
@@ -167,7 +167,7 @@ def test_sigc_medium_shapes_sampled(N):
     Zc = z_block(47, 2, 0, n_pb, n_band, n_qp, 200.0)
     e_qp = np.sort(rng.uniform(-0.3, 0.4, n_qp))
     e_band = np.sort(rng.uniform(-0.8, 3.0, n_band))
-    ctx = N.qsgw_sigc_init(n_qp, n_pb, om, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_sigc_init(n_qp, n_pb, om, N.QSGW_MIXED_F16X3)
     try:
         Zd, eq, eb = _dev(Zc), _dev(e_qp), _dev(e_band)
         Wd = _dev(np.ascontiguousarray(Wc.transpose(0, 2, 1)))

@@ -68,17 +68,17 @@ def test_sigx_fp64_parity_and_host_staging(N):
 def test_sigx_mixed_parity_ragged(N, n_qp, occ, n_pb):
     blocks = _blocks(n_qp, occ, n_pb)
     ref = _oracle(blocks, occ, n_pb)
-    got = _run(N, N.QSGW_MIXED_BF16X3, n_qp, occ, n_pb, blocks)
+    got = _run(N, N.QSGW_MIXED_F16X3, n_qp, occ, n_pb, blocks)
     assert rel_fro(got, ref) <= 1e-6, rel_fro(got, ref)
     d = np.sqrt(np.abs(np.diag(ref)))
     assert np.all(np.abs(got - ref) <= 1e-6 * np.outer(d, d) + 1e-300)
     assert np.array_equal(got, got.conj().T)
-    assert np.array_equal(_run(N, N.QSGW_MIXED_BF16X3, n_qp, occ, n_pb, blocks, mode="c64"), got)
+    assert np.array_equal(_run(N, N.QSGW_MIXED_F16X3, n_qp, occ, n_pb, blocks, mode="c64"), got)
 
 
 def test_sigx_nonpositive_v_is_reported(N):
     n_qp, n_pb = 16, 8
-    ctx = N.qsgw_sigx_init([n_qp], N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_sigx_init([n_qp], N.QSGW_MIXED_F16X3)
     try:
         zt = z_block(3, 0, 0, n_qp, 2, n_pb, 40.0)
         v = coulomb_v(3, 0, n_pb)
@@ -119,7 +119,7 @@ def test_sigx_paper_size_sampled(N):
     from synthetic import z_rows
     n_qp, n_pb, n_occ, n_k, seed = 428, 3139, 276, 16, 1
     rows = np.array([0, 101, 300, 427])
-    ctx = N.qsgw_sigx_init([n_qp], N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_sigx_init([n_qp], N.QSGW_MIXED_F16X3)
     try:
         Z = torch.empty((n_occ * n_pb, n_qp), dtype=torch.complex128, device="cuda")
         for k in range(n_k):

@@ -74,7 +74,7 @@ def _oracle_S(blocks, edges=EDGES):
     return oracle.hist_spectral(Z, Z, d, edges)
 
 
-@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_BF16X3", 1e-6)])
+@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_F16X3", 1e-6)])
 @pytest.mark.parametrize("n,shapes", [(70, [(5, 130), (3, 61)]), (130, [(9, 300)])])
 def test_spectral_weights_and_real_axis(N, prec_name, tol, n, shapes):
     blocks = _blocks(n, shapes)
@@ -100,8 +100,8 @@ def test_spectral_weights_and_real_axis(N, prec_name, tol, n, shapes):
 def test_spectral_deterministic_and_errors(N):
     n = 64
     blocks = _blocks(n, [(4, 90), (2, 45)])
-    a, _ = _gpu_S(N, N.QSGW_MIXED_BF16X3, n, blocks)
-    b, _ = _gpu_S(N, N.QSGW_MIXED_BF16X3, n, blocks)
+    a, _ = _gpu_S(N, N.QSGW_MIXED_F16X3, n, blocks)
+    b, _ = _gpu_S(N, N.QSGW_MIXED_F16X3, n, blocks)
     assert np.array_equal(a, b)
     ctx = N.qsgw_spectral_init(n, EDGES, N.QSGW_FP64)
     try:
@@ -130,7 +130,7 @@ def test_spectral_many_sparse_bins(N):
     blocks = _blocks(600, [(20, 90), (12, 100)], seed=23)
     ref, _ = _oracle_S(blocks, edges)
     assert sum(np.linalg.norm(r) > 0 for r in ref) > 64
-    S, _ = _gpu_S(N, N.QSGW_MIXED_BF16X3, 600, blocks, edges=edges)
+    S, _ = _gpu_S(N, N.QSGW_MIXED_F16X3, 600, blocks, edges=edges)
     for j in range(ref.shape[0]):
         nrm = np.linalg.norm(ref[j])
         if nrm == 0.0:
@@ -142,7 +142,7 @@ def test_spectral_many_sparse_bins(N):
 STAGE_EDGES = np.array([0.05, 0.6, 1.0, 1.5, 4.0])  # 4 wide bins: thousands of columns per bin and call
 
 
-@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_BF16X3", 1e-6)])
+@pytest.mark.parametrize("prec_name,tol", [("QSGW_FP64", 1e-12), ("QSGW_MIXED_F16X3", 1e-6)])
 def test_spectral_staging_paths(N, prec_name, tol):
     """The per-bin staging (4096 columns) on all its paths, against the oracle. Bin 3 takes 5277
     columns in call 0 (more than its staging: updated at once), 1973 in call 1 (staged), 2787 in
@@ -176,7 +176,7 @@ def test_spectral_reset_drops_staged_columns(N):
     of bin 2 and block 1, bin 2 holds block 1 alone and the other bins both blocks."""
     n = 48
     blocks = _blocks(n, [(10, 300), (16, 250)], seed=29)
-    ctx = N.qsgw_spectral_init(n, STAGE_EDGES, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_spectral_init(n, STAGE_EDGES, N.QSGW_MIXED_F16X3)
     try:
         keep = []
         for i, (zt, eo, eu, no, nu) in enumerate(blocks):
@@ -220,7 +220,7 @@ def test_realaxis_medium_full_size_sampled(N):
     nb = edges.size - 1
     rows = np.array([0, 17, 700, 1250, 1499])
     bins_out = [30, 80, 120, 150]
-    ctx = N.qsgw_spectral_init(n, edges, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_spectral_init(n, edges, N.QSGW_MIXED_F16X3)
     try:
         Z = torch.empty((no * nu, n), dtype=torch.complex128, device="cuda")
         for k in range(nk):

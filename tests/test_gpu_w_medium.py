@@ -43,7 +43,7 @@ def case():
     return dict(zt=zt, eo=eo, eu=eu, v=v, chi=chi, W=Wref)
 
 
-@pytest.mark.parametrize("prec_name", ["QSGW_FP64", "QSGW_MIXED_BF16X3"])
+@pytest.mark.parametrize("prec_name", ["QSGW_FP64", "QSGW_MIXED_F16X3"])
 def test_chi0_and_w_at_npb_1500(N, case, prec_name):
     L = W.n_omega
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()

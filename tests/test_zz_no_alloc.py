@@ -49,7 +49,7 @@ def _oracle_chi0(q, n_pb, n_occ, n_unocc, L):
 
 
 def _context_chi0(N, Z, eo, eu, n_pb, n_occ, n_unocc, om):
-    ctx = N.qsgw_chi0_init([n_pb], om, 2.0, N.QSGW_MIXED_BF16X3)
+    ctx = N.qsgw_chi0_init([n_pb], om, 2.0, N.QSGW_MIXED_F16X3)
     try:
         N.qsgw_chi0_accumulate(ctx, 0, Z, n_pb, n_occ, n_unocc, eo, eu, om)
         chi = torch.empty((len(om), n_pb, n_pb), dtype=torch.complex128, device="cuda")
