@@ -96,6 +96,8 @@ struct qsgw_ctx {
   size_t pbuf_cap = 0;
   void* d_cbuf = nullptr;
   size_t cbuf_cap = 0;
+  void* d_dig = nullptr;  // digit images of the update on the tensor cores (mixed contexts)
+  size_t dig_cap = 0;
   int* d_info = nullptr;
 };
 
@@ -637,6 +639,8 @@ qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps
   qsgw_status st = grow(&c->d_sbuf, &c->sbuf_cap, sizeof(double2) * 32 * 32 * L);
   if (st == QSGW_OK) st = grow(&c->d_pbuf, &c->pbuf_cap, sizeof(double2) * 32 * (size_t)n * L);
   if (st == QSGW_OK) st = grow(&c->d_cbuf, &c->cbuf_cap, sizeof(double2) * 32 * (size_t)n * L);
+  const bool tc = c->prec == QSGW_MIXED_F16X3;  // the update on the tensor cores, at FP64 accuracy
+  if (st == QSGW_OK && tc) st = grow(&c->d_dig, &c->dig_cap, eps_inverse_digit_bytes(n, L));
   if (st != QSGW_OK) return st;
 
   launch_form_eps(a.acc, c->prec == QSGW_FP64 ? ACC_FP64 : ACC_DF32, n, a.n_pad, L, c->spin, v, w, c->stream);
@@ -644,7 +648,8 @@ qsgw_status qsgw_eps_inv(qsgw_ctx* c, int q, const double* v, void* W, void* eps
   if (eps_out) QSGW_CK(cudaMemcpyAsync(eps_out, w, sizeof(double2) * nn * L, cudaMemcpyDeviceToDevice, c->stream));
   QSGW_CK(cudaMemsetAsync(c->d_info, 0, sizeof(int) * kMaxOmega, c->stream));
   launch_eps_inverse(w, n, L, static_cast<double2*>(c->d_sbuf), static_cast<double2*>(c->d_pbuf),
-                     static_cast<double2*>(c->d_cbuf), c->d_info, c->stream);
+                     static_cast<double2*>(c->d_cbuf), tc ? static_cast<uint8_t*>(c->d_dig) : nullptr, c->d_info,
+                     c->d_err, c->stream);
   QSGW_CK(cudaGetLastError());
   launch_w_from_inverse(w, n, L, v, correlation_only, -1.0, c->stream);  // the sweep leaves -eps^{-1}
   QSGW_CK(cudaGetLastError());
@@ -694,7 +699,7 @@ qsgw_status qsgw_chi0_destroy(qsgw_ctx* c) {
   }
   if (c->cstream) cudaStreamDestroy(c->cstream);
   mixed_free(c->mixed);
-  for (void* p : {c->d_sbuf, c->d_pbuf, c->d_cbuf})
+  for (void* p : {c->d_sbuf, c->d_pbuf, c->d_cbuf, c->d_dig})
     if (p) cudaFree(p);
   if (c->d_info) cudaFree(c->d_info);
   if (c->d_err) cudaFree(c->d_err);

@@ -17,10 +17,25 @@
 // trailing matrix of a right-looking Cholesky shrinks, and its last steps leave most SMs idle).
 //
 // GB300 runs FP64 on the CUDA cores at ~1.2 TFLOP/s with DFMA (faster than its FP64 MMA, ~1.05
-// TFLOP/s, both measured), so the update is a DFMA register-tile kernel: 64 x 64 output tiles,
-// 4 x 4 complex accumulators per thread, operands staged in shared memory. Only the lower triangle
-// of A is read or written (element (I, J), I >= J, at J * n + I of each frequency's matrix).
+// TFLOP/s, both measured). The update, 95 % of the flops, therefore runs on the tcgen05 tensor
+// cores in exact integer arithmetic that reproduces FP64 accuracy:
+//   every row of P and of C (32 complex values) is put on a power-of-two grid, x 2^e with
+//   max |x 2^e| <= 127, and cut into 7 integer digits, x 2^e = sum_s d_s 2^(-8 s), |d_s| <= 128
+//   (each an exact FP16 value), with a remainder below 2^-49 of the row maximum;
+//   the product of level L = i + j (digits i of P, j of C, L <= 6) is a sum of 64 products of
+//   integers below 2^14 per pair, at most 7 * 64 * 128^2 < 2^24 over the pairs of a level, so
+//   each level accumulates exactly in its own FP32 TMEM accumulator whatever the rounding mode;
+//   the levels are combined in FP64, sum_L acc_L 2^(-8 L), and scaled by 2^(-eP - eC).
+// The dropped levels (i + j >= 7) and the digit remainders are below 2^-52 of |P|max |C|max per
+// product, so the update carries FP64 accuracy (the error is relative to the sum of the terms'
+// magnitudes, as for an FP64 product). 28 digit pairs x 4 K-steps = 112 MMAs (M = 128: 64 rows
+// times (Re, Im); N = 64; K = 16) per 64 x 64 tile and frequency. The mixed-precision contexts use
+// it; the plain FP64 contexts keep the DFMA update kernel. Only the lower triangle of A is read or
+// written (element (I, J), I >= J, at J * n + I of each frequency's matrix).
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace qsgw {
 
@@ -221,16 +236,234 @@ __global__ void __launch_bounds__(256) sweep_update_kernel(double2* __restrict__
     }
 }
 
-void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, double2* cbuf, int* d_info,
-                        cudaStream_t s) {
+// ------------------------------------------------------------------ the update on the tensor cores
+constexpr int DL = 7;                       // integer digits per value, and digit levels kept
+constexpr int DIG_A = 128 * 2 * SB * 2;     // bytes of one level of a P row-tile image (M = 128, K' = 64): 16 KB
+constexpr int DIG_B = ST * 2 * SB * 2;      // bytes of one level of a C column-tile image (N = 64): 8 KB
+constexpr int IMG_A = DL * DIG_A;           // 112 KB
+constexpr int IMG_B = DL * DIG_B;           // 56 KB
+constexpr uint64_t kTcWaitNs = 1000000000ull;
+
+size_t eps_inverse_digit_bytes(int n, int L) {
+  const size_t ntr = (size_t)(n + ST - 1) / ST;
+  return (size_t)L * ntr * (IMG_A + IMG_B) + 2 * sizeof(int) * (size_t)L * ntr * ST;
+}
+
+// Grid (64-row tiles, frequency, side): side 0 cuts the rows of P into the A-operand image of the
+// tile ([level][k-group 8][row group 16][8 rows][8 K'] FP16: Re rows (Pr, Pi), Im rows (Pi, -Pr) along
+// K' = 2 c + (0, 1)), side 1 the rows of C into the B-operand image ([level][k-group 8][row group 8]
+// [8 rows][8 K']: (Cr, Ci)), each with the row's grid exponent (e with max |x 2^e| <= 127). Values of
+// columns c >= bk, rows past n and the rows of the pivot block (zero in P and C) give zero digits.
+__global__ void __launch_bounds__(256) sweep_digits_kernel(int n, int bk, const double2* __restrict__ pbuf,
+                                                           const double2* __restrict__ cbuf,
+                                                           uint8_t* __restrict__ imgA, uint8_t* __restrict__ imgB,
+                                                           int* __restrict__ eP, int* __restrict__ eC) {
+  const int tr = blockIdx.x, l = blockIdx.y, side = blockIdx.z, t = threadIdx.x;
+  const int ntr = gridDim.x;
+  const int r = t & (ST - 1), q = t >> 6;  // row of the tile, quarter of the columns (8 of 32)
+  const int i = tr * ST + r;
+  const double2* src = (side == 0 ? pbuf : cbuf) + (size_t)l * SB * n;
+  __shared__ double red[4][ST];
+  double2 v[8];
+  double m = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int c = q * 8 + k;
+    v[k] = (i < n && c < bk) ? src[(size_t)c * n + i] : make_double2(0.0, 0.0);
+    m = fmax(m, fmax(fabs(v[k].x), fabs(v[k].y)));
+  }
+  red[q][r] = m;
+  __syncthreads();
+  m = fmax(fmax(red[0][r], red[1][r]), fmax(red[2][r], red[3][r]));
+  int e = 0;
+  if (m > 0.0 && isfinite(m)) {
+    int E;
+    frexp(m, &E);  // m = f 2^E, f in [0.5, 1): m 2^(7 - E) in [64, 128)
+    e = 7 - E;
+    if (ldexp(m, e) > 127.0) --e;
+    e = max(-1000, min(1000, e));
+  }
+  if (q == 0 && i < ntr * ST) (side == 0 ? eP : eC)[(size_t)l * ntr * ST + i] = e;
+  // digits, level by level: t <- (t - rint(t)) * 256 is exact in FP64
+  double tr_[8], ti_[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    tr_[k] = ldexp(v[k].x, e);
+    ti_[k] = ldexp(v[k].y, e);
+  }
+  uint8_t* img = side == 0 ? imgA + ((size_t)l * ntr + tr) * IMG_A : imgB + ((size_t)l * ntr + tr) * IMG_B;
+  for (int lev = 0; lev < DL; ++lev) {
+    __half dr[8], di[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double a = rint(tr_[k]), b = rint(ti_[k]);
+      dr[k] = __double2half(a);  // integers of magnitude <= 128: exact
+      di[k] = __double2half(b);
+      tr_[k] = (tr_[k] - a) * 256.0;
+      ti_[k] = (ti_[k] - b) * 256.0;
+    }
+    // this thread's 8 complex columns are k-groups 2q and 2q + 1 (4 columns, 8 K' values each)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int kg = 2 * q + h;
+      __half re[8], im[8];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        re[2 * k] = dr[4 * h + k];
+        re[2 * k + 1] = di[4 * h + k];
+        im[2 * k] = di[4 * h + k];
+        im[2 * k + 1] = __hneg(dr[4 * h + k]);
+      }
+      if (side == 0) {
+        uint8_t* base = img + lev * DIG_A + kg * 2048;
+        *reinterpret_cast<uint4*>(base + (r >> 3) * 128 + (r & 7) * 16) = *reinterpret_cast<const uint4*>(re);
+        const int mi = ST + r;
+        *reinterpret_cast<uint4*>(base + (mi >> 3) * 128 + (mi & 7) * 16) = *reinterpret_cast<const uint4*>(im);
+      } else {
+        uint8_t* base = img + lev * DIG_B + kg * 1024;
+        *reinterpret_cast<uint4*>(base + (r >> 3) * 128 + (r & 7) * 16) = *reinterpret_cast<const uint4*>(re);
+      }
+    }
+  }
+}
+
+// Grid (lower 64 x 64 tiles, frequency), 128 threads, one CTA per SM (168 KB of operand images, 448
+// TMEM columns). One thread moves the two images with bulk copies and issues the 112 MMAs; the four
+// warps then read their TMEM lane quarter (lane m: row I = m mod 64 of the tile, Re part for m < 64
+// and Im part above), combine the 7 levels in FP64 and update their half of each element: the same
+// element rules as sweep_update_kernel. Every wait is bounded (1 s); a wait that gives up sets
+// DEV_TIMEOUT, issues no MMA and leaves the tile unchanged.
+__global__ void __launch_bounds__(128, 1) sweep_update_tc_kernel(double2* __restrict__ w, int n, int k0, int bk,
+                                                                 const double2* __restrict__ pbuf,
+                                                                 const uint8_t* __restrict__ imgA,
+                                                                 const uint8_t* __restrict__ imgB,
+                                                                 const int* __restrict__ eP,
+                                                                 const int* __restrict__ eC, int* d_err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + IMG_A;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + IMG_B);  // [0] operands landed, [1] MMAs done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  int* sok = reinterpret_cast<int*>(tmem_slot + 1);
+  const int l = blockIdx.y, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  int ti = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);  // lower tile (ti, tj), ti >= tj
+  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
+  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
+  const int tj = blockIdx.x - ti * (ti + 1) / 2;
+  const int ntr = (n + ST - 1) / ST;
+  if (t == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    *sok = 1;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (t == 0) {
+    mbar_arrive_expect_tx(&bars[0], IMG_A + IMG_B);
+    bulk_g2s(sA, imgA + ((size_t)l * ntr + ti) * IMG_A, IMG_A, &bars[0]);
+    bulk_g2s(sB, imgB + ((size_t)l * ntr + tj) * IMG_B, IMG_B, &bars[0]);
+    bool ok = mbar_wait_bounded(&bars[0], 0, kTcWaitNs);
+    if (ok) {
+      tc_fence_after();
+      const uint32_t idesc = make_idesc_f16_f32(128, ST);
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      for (int lev = 0; lev < DL; ++lev) {
+        uint32_t acc = 0;
+        for (int i = 0; i <= lev; ++i) {
+          const int j = lev - i;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint64_t ad = make_smem_desc(a0 + i * DIG_A + ks * 4096, 2048, 128, 0);
+            const uint64_t bd = make_smem_desc(b0 + j * DIG_B + ks * 2048, 16 * ST, 128, 0);
+            mma_f16(tmem + lev * ST, ad, bd, idesc, acc);
+            acc = 1;
+          }
+        }
+      }
+    } else {
+      atomicCAS(d_err, DEV_OK, DEV_TIMEOUT);
+      *sok = 0;
+      mbar_wait_bounded(&bars[0], 0, kTcWaitNs);  // give the copies in flight a last chance to land
+    }
+    mma_commit(&bars[1]);  // arrives once the MMAs (if any) are done
+  }
+  __syncwarp();
+  const bool done = mbar_wait_bounded(&bars[1], 0, kTcWaitNs);
+  if (!done && lane == 0) atomicCAS(d_err, DEV_OK, DEV_TIMEOUT);
+  tc_fence_after();
+  __syncthreads();  // *sok is final
+  if (*sok && __all_sync(0xffffffffu, done)) {
+    double2* m = w + (size_t)l * n * n;
+    const double2* P = pbuf + (size_t)l * SB * n;
+    const int row = t & (ST - 1), part = t >> 6;  // TMEM lane t: row of the tile, Re (0) or Im (1)
+    const int I = ti * ST + row;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const int e_i = eP[(size_t)l * ntr * ST + I];
+    for (int c0 = 0; c0 < ST; c0 += 8) {
+      uint32_t r[DL][8];
+#pragma unroll
+      for (int lev = 0; lev < DL; ++lev) tmem_ld_x8(tl + lev * ST + c0, r[lev]);
+      tmem_ld_wait();
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int J = tj * ST + c0 + jj;
+        if (I >= n || J >= n || I < J) continue;
+        const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
+        if (inI && inJ) continue;
+        double2* o = m + (size_t)J * n + I;
+        if (inJ || inI) {  // the pivot block's column and row take P (the Re thread writes both parts)
+          if (part == 0) *o = inJ ? P[(size_t)(J - k0) * n + I] : conj2(P[(size_t)(I - k0) * n + J]);
+          continue;
+        }
+        double acc = 0.0;
+#pragma unroll
+        for (int lev = DL - 1; lev >= 0; --lev) acc = fma(acc, 0.00390625, (double)__uint_as_float(r[lev][jj]));
+        const double val = ldexp(acc, -e_i - eC[(size_t)l * ntr * ST + J]);
+        double* half_ = reinterpret_cast<double*>(o) + part;
+        *half_ -= val;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+static size_t tc_update_smem() { return 1024 + IMG_A + IMG_B + 64; }
+
+void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, double2* cbuf, uint8_t* dig,
+                        int* d_info, int* d_err, cudaStream_t s) {
   const int nt = (n + ST - 1) / ST;
   const int tiles = nt * (nt + 1) / 2;
+  if (dig)  // the attribute belongs to the current context: set it on every call
+    cudaFuncSetAttribute(sweep_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_update_smem());
+  uint8_t* imgA = dig;
+  uint8_t* imgB = imgA + (size_t)L * nt * IMG_A;
+  int* eP = reinterpret_cast<int*>(imgB + (size_t)L * nt * IMG_B);
+  int* eC = eP + (size_t)L * nt * ST;
   for (int k0 = 0; k0 < n; k0 += SB) {
     const int bk = n - k0 < SB ? n - k0 : SB;
     sweep_pivot_kernel<<<L, 256, 0, s>>>(w, n, k0, bk, sbuf, d_info);
     if (n <= bk) break;  // a single block: nothing outside it
     sweep_panel_kernel<<<dim3((n + SP - 1) / SP, L), 256, 0, s>>>(w, n, k0, bk, sbuf, pbuf, cbuf);
-    sweep_update_kernel<<<dim3(tiles, L), 256, 0, s>>>(w, n, k0, bk, pbuf, cbuf);
+    if (dig) {
+      sweep_digits_kernel<<<dim3(nt, L, 2), 256, 0, s>>>(n, bk, pbuf, cbuf, imgA, imgB, eP, eC);
+      sweep_update_tc_kernel<<<dim3(tiles, L), 128, tc_update_smem(), s>>>(w, n, k0, bk, pbuf, imgA, imgB, eP, eC,
+                                                                           d_err);
+    } else {
+      sweep_update_kernel<<<dim3(tiles, L), 256, 0, s>>>(w, n, k0, bk, pbuf, cbuf);
+    }
   }
 }
 

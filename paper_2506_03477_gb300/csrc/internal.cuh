@@ -71,10 +71,13 @@ void launch_w_from_inverse(double2* w, int n, int L, const double* v, int wc, do
 // ---- eps^{-1} (epsinv.cu)
 // In place on w ([L][n][n], column-major; the lower triangle of each Hermitian positive definite
 // matrix is read): the lower triangle becomes -eps^{-1}. sbuf: [L][32][32], pbuf and cbuf:
-// [L][32][n] complex128 scratch. d_info[l] (zeroed by the caller) receives the 1-based index of the
-// first non-positive pivot, as a Cholesky factorisation would report it.
-void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, double2* cbuf, int* d_info,
-                        cudaStream_t s);
+// [L][32][n] complex128 scratch. dig: eps_inverse_digit_bytes(n, L) bytes of scratch for the
+// update on the tensor cores (FP64 accuracy from exact integer digits), or null for the plain DFMA
+// update. d_info[l] (zeroed by the caller) receives the 1-based index of the first non-positive
+// pivot, as a Cholesky factorisation would report it; a bounded wait that gave up sets d_err.
+size_t eps_inverse_digit_bytes(int n, int L);
+void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, double2* cbuf, uint8_t* dig,
+                        int* d_info, int* d_err, cudaStream_t s);
 
 // ---- real-axis route (spectral.cu)
 // Bin every column by Delta (edges: device [n_bins + 1]), count per bin, exclusive offsets

@@ -5,7 +5,9 @@ scaled by 64 stands in for all 64 k-points: chi0 then has the magnitude of the f
 eps has its conditioning, which is what the accuracy of W depends on. Bars: plain FP64 chi0
 <= 1e-12 and W <= 1e-10 relative Frobenius; mixed chi0 <= 1e-6 relative Frobenius and diag W
 <= 1e-6 relative, per frequency. The FP64 eps^{-1} (block sweep with Cholesky pivots) runs in
-both precisions, here on 47 pivot blocks with a ragged last one (1500 = 46 * 32 + 28)."""
+both precisions, here on 47 pivot blocks with a ragged last one (1500 = 46 * 32 + 28); in the mixed
+precision its updates run on the tensor cores, checked at 1e-10 against the oracle's inverse of the
+GPU's own chi0."""
 import numpy as np
 import pytest
 
@@ -70,3 +72,10 @@ def test_chi0_and_w_at_npb_1500(N, case, prec_name):
         else:
             assert e_chi <= 1e-6 and e_dw <= 1e-6, (l, e_chi, e_w, e_dw)
         assert np.array_equal(Wg[l], Wg[l].conj().T)
+    if not fp64:
+        # the inverse itself (its updates on the tensor cores in exact integer digits) at FP64
+        # accuracy: against the oracle's inverse of the GPU's own chi0
+        _, Wown, _, info = oracle.eps_w(chi, case["v"], want_eps=False, want_wc=False)
+        assert np.all(info == 0)
+        for l in range(L):
+            assert rel_fro(Wg[l], Wown[l]) <= 1e-10, (l, rel_fro(Wg[l], Wown[l]))
