@@ -281,26 +281,36 @@ __global__ void __launch_bounds__(256) sweep_digits_kernel(int n, int bk, const 
     frexp(m, &E);  // m = f 2^E, f in [0.5, 1): m 2^(7 - E) in [64, 128)
     e = 7 - E;
     if (ldexp(m, e) > 127.0) --e;
-    e = max(-1000, min(1000, e));
+    e = max(-400, min(400, e));  // keeps 2^(-16 - eP - eC) and 2^(-48 - eP - eC) normal doubles
   }
   if (q == 0 && i < ntr * ST) (side == 0 ? eP : eC)[(size_t)l * ntr * ST + i] = e;
-  // digits, level by level: t <- (t - rint(t)) * 256 is exact in FP64
-  double tr_[8], ti_[8];
+  // x 2^e on the grid of 2^-48, as an exact 56-bit integer (|x 2^e| <= 127; rint drops below 2^-49),
+  // then 7 balanced base-256 digits from the bottom: d = the low byte as a signed value in
+  // [-128, 127], T <- (T - d) / 256; the last (leading) digit is in [-128, 128].
+  const double g = ldexp(1.0, e + 48);
+  long long Tr[8], Ti[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    tr_[k] = ldexp(v[k].x, e);
-    ti_[k] = ldexp(v[k].y, e);
+    Tr[k] = __double2ll_rn(v[k].x * g);
+    Ti[k] = __double2ll_rn(v[k].y * g);
   }
   uint8_t* img = side == 0 ? imgA + ((size_t)l * ntr + tr) * IMG_A : imgB + ((size_t)l * ntr + tr) * IMG_B;
-  for (int lev = 0; lev < DL; ++lev) {
+  for (int lev = DL - 1; lev >= 0; --lev) {
     __half dr[8], di[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const double a = rint(tr_[k]), b = rint(ti_[k]);
-      dr[k] = __double2half(a);  // integers of magnitude <= 128: exact
-      di[k] = __double2half(b);
-      tr_[k] = (tr_[k] - a) * 256.0;
-      ti_[k] = (ti_[k] - b) * 256.0;
+      long long a, b;
+      if (lev > 0) {
+        a = ((Tr[k] + 128) & 255) - 128;
+        b = ((Ti[k] + 128) & 255) - 128;
+        Tr[k] = (Tr[k] - a) >> 8;  // exact: T - a is a multiple of 256
+        Ti[k] = (Ti[k] - b) >> 8;
+      } else {
+        a = Tr[k];
+        b = Ti[k];
+      }
+      dr[k] = __int2half_rn((int)a);  // integers of magnitude <= 128: exact
+      di[k] = __int2half_rn((int)b);
     }
     // this thread's 8 complex columns are k-groups 2q and 2q + 1 (4 columns, 8 K' values each)
 #pragma unroll
@@ -327,18 +337,19 @@ __global__ void __launch_bounds__(256) sweep_digits_kernel(int n, int bk, const 
   }
 }
 
-// Grid (lower 64 x 64 tiles, frequency), 128 threads, one CTA per SM (168 KB of operand images, 448
-// TMEM columns). One thread moves the two images with bulk copies and issues the 112 MMAs; the four
-// warps then read their TMEM lane quarter (lane m: row I = m mod 64 of the tile, Re part for m < 64
-// and Im part above), combine the 7 levels in FP64 and update their half of each element: the same
-// element rules as sweep_update_kernel. Every wait is bounded (1 s); a wait that gives up sets
-// DEV_TIMEOUT, issues no MMA and leaves the tile unchanged.
-__global__ void __launch_bounds__(128, 1) sweep_update_tc_kernel(double2* __restrict__ w, int n, int k0, int bk,
-                                                                 const double2* __restrict__ pbuf,
-                                                                 const uint8_t* __restrict__ imgA,
-                                                                 const uint8_t* __restrict__ imgB,
-                                                                 const int* __restrict__ eP,
-                                                                 const int* __restrict__ eC, int* d_err) {
+// Grid (lower 64 x 64 tiles, frequency), 512 threads, one CTA per SM (168 KB of operand images, 448
+// TMEM columns). One thread moves the two images with bulk copies and issues the 112 MMAs; the 16
+// warps then read TMEM (warp w: lane quarter w mod 4, i.e. lane m = row m mod 64 of the tile, Re part
+// for m < 64 and Im part above; columns 16 (w / 4) .. + 16), combine the 7 levels and update their
+// half of each element: the same element rules as sweep_update_kernel. Every wait is bounded (1 s);
+// a wait that gives up sets DEV_TIMEOUT, issues no MMA and leaves the tile unchanged.
+constexpr int TC_THREADS = 512;
+__global__ void __launch_bounds__(TC_THREADS, 1) sweep_update_tc_kernel(double2* __restrict__ w, int n, int k0, int bk,
+                                                                        const double2* __restrict__ pbuf,
+                                                                        const uint8_t* __restrict__ imgA,
+                                                                        const uint8_t* __restrict__ imgB,
+                                                                        const int* __restrict__ eP,
+                                                                        const int* __restrict__ eC, int* d_err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -346,6 +357,7 @@ __global__ void __launch_bounds__(128, 1) sweep_update_tc_kernel(double2* __rest
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + IMG_B);  // [0] operands landed, [1] MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   int* sok = reinterpret_cast<int*>(tmem_slot + 1);
+  int* sE = sok + 1;  // [64] grid exponents of the tile's rows (P), [64] of its columns (C)
   const int l = blockIdx.y, t = threadIdx.x, warp = t >> 5, lane = t & 31;
   int ti = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);  // lower tile (ti, tj), ti >= tj
   while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
@@ -358,6 +370,8 @@ __global__ void __launch_bounds__(128, 1) sweep_update_tc_kernel(double2* __rest
     *sok = 1;
     fence_mbar_init();
   }
+  if (t < 2 * ST)
+    sE[t] = t < ST ? eP[(size_t)l * ntr * ST + ti * ST + t] : eC[(size_t)l * ntr * ST + tj * ST + t - ST];
   if (warp == 0) {
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
@@ -403,32 +417,52 @@ __global__ void __launch_bounds__(128, 1) sweep_update_tc_kernel(double2* __rest
   if (*sok && __all_sync(0xffffffffu, done)) {
     double2* m = w + (size_t)l * n * n;
     const double2* P = pbuf + (size_t)l * SB * n;
-    const int row = t & (ST - 1), part = t >> 6;  // TMEM lane t: row of the tile, Re (0) or Im (1)
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int lm = quarter * 32 + lane;       // TMEM lane: row of the tile, Re (< 64) or Im part
+    const int row = lm & (ST - 1), part = lm >> 6;
     const int I = ti * ST + row;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    const int e_i = eP[(size_t)l * ntr * ST + I];
-    for (int c0 = 0; c0 < ST; c0 += 8) {
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int e_i = sE[row];
+    for (int c0 = cg * 16; c0 < cg * 16 + 16; c0 += 8) {
       uint32_t r[DL][8];
 #pragma unroll
       for (int lev = 0; lev < DL; ++lev) tmem_ld_x8(tl + lev * ST + c0, r[lev]);
       tmem_ld_wait();
+      double val[8], old[8];
+      bool upd[8];
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
         const int J = tj * ST + c0 + jj;
-        if (I >= n || J >= n || I < J) continue;
         const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
-        if (inI && inJ) continue;
-        double2* o = m + (size_t)J * n + I;
-        if (inJ || inI) {  // the pivot block's column and row take P (the Re thread writes both parts)
-          if (part == 0) *o = inJ ? P[(size_t)(J - k0) * n + I] : conj2(P[(size_t)(I - k0) * n + J]);
-          continue;
-        }
-        double acc = 0.0;
+        upd[jj] = I < n && J < n && I >= J && !inI && !inJ;
+        // the level sums are exact integers below 2^23: combine them exactly in two 64-bit words,
+        // hi = a0 2^16 + a1 2^8 + a2 and lo = a3 2^24 + a4 2^16 + a5 2^8 + a6, so that the value is
+        // (hi 2^-16 + lo 2^-48) 2^(-eP - eC), with two roundings in FP64
+        long long a[DL];
 #pragma unroll
-        for (int lev = DL - 1; lev >= 0; --lev) acc = fma(acc, 0.00390625, (double)__uint_as_float(r[lev][jj]));
-        const double val = ldexp(acc, -e_i - eC[(size_t)l * ntr * ST + J]);
-        double* half_ = reinterpret_cast<double*>(o) + part;
-        *half_ -= val;
+        for (int lev = 0; lev < DL; ++lev) a[lev] = __float2int_rn(__uint_as_float(r[lev][jj]));
+        const long long hi = a[0] * 65536LL + a[1] * 256LL + a[2];
+        const long long lo = a[3] * 16777216LL + a[4] * 65536LL + a[5] * 256LL + a[6];
+        const int ee = e_i + sE[ST + c0 + jj];  // |ee| <= 800: both factors are normal doubles
+        const double c_hi = __longlong_as_double((long long)(1023 - 16 - ee) << 52);
+        const double c_lo = __longlong_as_double((long long)(1023 - 48 - ee) << 52);
+        val[jj] = fma((double)lo, c_lo, (double)hi * c_hi);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)  // the loads first, all independent
+        old[jj] = upd[jj] ? reinterpret_cast<const double*>(m + (size_t)(tj * ST + c0 + jj) * n + I)[part] : 0.0;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (upd[jj]) reinterpret_cast<double*>(m + (size_t)(tj * ST + c0 + jj) * n + I)[part] = old[jj] - val[jj];
+      if (part == 0) {  // the pivot block's column and row take P (the Re thread writes both parts)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int J = tj * ST + c0 + jj;
+          if (I >= n || J >= n || I < J) continue;
+          const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
+          if (inI == inJ) continue;
+          m[(size_t)J * n + I] = inJ ? P[(size_t)(J - k0) * n + I] : conj2(P[(size_t)(I - k0) * n + J]);
+        }
       }
     }
   }
@@ -440,7 +474,7 @@ __global__ void __launch_bounds__(128, 1) sweep_update_tc_kernel(double2* __rest
   }
 }
 
-static size_t tc_update_smem() { return 1024 + IMG_A + IMG_B + 64; }
+static size_t tc_update_smem() { return 1024 + IMG_A + IMG_B + 64 + 2 * ST * sizeof(int); }
 
 void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, double2* cbuf, uint8_t* dig,
                         int* d_info, int* d_err, cudaStream_t s) {
@@ -459,8 +493,8 @@ void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, 
     sweep_panel_kernel<<<dim3((n + SP - 1) / SP, L), 256, 0, s>>>(w, n, k0, bk, sbuf, pbuf, cbuf);
     if (dig) {
       sweep_digits_kernel<<<dim3(nt, L, 2), 256, 0, s>>>(n, bk, pbuf, cbuf, imgA, imgB, eP, eC);
-      sweep_update_tc_kernel<<<dim3(tiles, L), 128, tc_update_smem(), s>>>(w, n, k0, bk, pbuf, imgA, imgB, eP, eC,
-                                                                           d_err);
+      sweep_update_tc_kernel<<<dim3(tiles, L), TC_THREADS, tc_update_smem(), s>>>(w, n, k0, bk, pbuf, imgA, imgB,
+                                                                                  eP, eC, d_err);
     } else {
       sweep_update_kernel<<<dim3(tiles, L), 256, 0, s>>>(w, n, k0, bk, pbuf, cbuf);
     }
