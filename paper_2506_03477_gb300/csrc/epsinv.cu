@@ -3,7 +3,7 @@
 // Cholesky. The paper keeps this inversion in double precision even in its mixed-precision mode.
 //
 // Sweep on pivot block k (rows and columns [k0, k0 + bk), bk <= 32), on the current matrix A:
-//   S     = A_kk^{-1}                    Cholesky A_kk = L L^H, S = L^{-H} L^{-1}
+//   S     = A_kk^{-1}                    Cholesky A_kk = L L^H, X = L^{-1}, S = X^H X
 //   A_ik <- A_ik S,  A_kj <- S A_kj      (i, j outside the block)
 //   A_ij <- A_ij - A_ik S A_kj           (i, j outside the block)
 //   A_kk <- -S
@@ -47,16 +47,17 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
 
-// One CTA per frequency: Cholesky of the pivot block, its inverse S (written whole to sbuf[l],
-// column-major SB x SB), and A_kk <- -S on the lower triangle. info[l] keeps the first
-// non-positive pivot (1-based global index); a failed pivot continues with 1 so the sweep runs to
-// its end, and that frequency's result is unspecified.
+// One CTA per frequency: Cholesky of the pivot block A_kk = L L^H and X = L^{-1} (lower triangular,
+// written whole to sbuf[l], column-major SB x SB, zeros above the diagonal). The panel kernel forms
+// S = X^H X from it. info[l] keeps the first non-positive pivot (1-based global index); a failed
+// pivot continues with 1 so the sweep runs to its end, and that frequency's result is unspecified.
 __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ w, int n, int k0, int bk,
                                                           double2* __restrict__ sbuf, int* __restrict__ info) {
   const int l = blockIdx.x, t = threadIdx.x;
   double2* m = w + (size_t)l * n * n;
   __shared__ double2 a[SB][SB + 1];  // a[i][j] = A(k0 + i, k0 + j), lower triangle
   __shared__ double2 x[SB][SB + 1];  // x = L^{-1}, lower triangle
+  __shared__ double rdiag[SB];       // 1 / L_ii
   __shared__ int fail;
   if (t == 0) fail = 0;
   for (int e = t; e < bk * bk; e += blockDim.x) {
@@ -72,7 +73,10 @@ __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ 
     }
     const double r = sqrt(d), ri = 1.0 / r;
     __syncthreads();  // every thread has read the pivot
-    if (t == 0) a[j][j] = make_double2(r, 0.0);
+    if (t == 0) {
+      a[j][j] = make_double2(r, 0.0);
+      rdiag[j] = ri;
+    }
     for (int i = j + 1 + t; i < bk; i += blockDim.x) {
       a[i][j].x *= ri;
       a[i][j].y *= ri;
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ 
   if (t < bk) {  // column t of L^{-1} by forward substitution
     const int j = t;
     for (int i = 0; i < j; ++i) x[i][j] = make_double2(0.0, 0.0);
-    x[j][j] = make_double2(1.0 / a[j][j].x, 0.0);
+    x[j][j] = make_double2(rdiag[j], 0.0);
     for (int i = j + 1; i < bk; ++i) {
       double sr = 0.0, si = 0.0;
       for (int c = j; c < i; ++c) {
@@ -100,42 +104,38 @@ __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ 
         sr = fma(u.x, v.x, fma(-u.y, v.y, sr));
         si = fma(u.x, v.y, fma(u.y, v.x, si));
       }
-      const double li = 1.0 / a[i][i].x;
-      x[i][j] = make_double2(-sr * li, -si * li);
+      x[i][j] = make_double2(-sr * rdiag[i], -si * rdiag[i]);
     }
   }
   __syncthreads();
-  double2* s = sbuf + (size_t)l * SB * SB;
-  for (int e = t; e < bk * bk; e += blockDim.x) {  // S = x^H x
-    const int i = e % bk, j = e / bk;
-    double sr = 0.0, si = 0.0;
-    for (int c = max(i, j); c < bk; ++c) {  // conj(x[c][i]) x[c][j]
-      const double2 u = x[c][i], v = x[c][j];
-      sr = fma(u.x, v.x, fma(u.y, v.y, sr));
-      si = fma(u.x, v.y, fma(-u.y, v.x, si));
-    }
-    if (i == j) si = 0.0;
-    s[j * SB + i] = make_double2(sr, si);
-    if (i >= j) m[(size_t)(k0 + j) * n + k0 + i] = make_double2(-sr, -si);
+  double2* xs = sbuf + (size_t)l * SB * SB;
+  for (int e = t; e < SB * SB; e += blockDim.x) {
+    const int i = e % SB, j = e / SB;
+    xs[j * SB + i] = (i < bk && j < bk) ? x[i][j] : make_double2(0.0, 0.0);
   }
   if (t == 0 && fail != 0 && info[l] == 0) info[l] = k0 + fail;
 }
 
 // Grid (row tiles of 32, frequency). C = column block k of A for rows outside the pivot block
-// (A(i, k0 + c), read from the lower triangle, conjugated above the block), P = C S. Both go to
-// column-major n x SB buffers: P for the update and the write-back, C as a copy, because the
-// update overwrites column and row k of A with P.
+// (A(i, k0 + c), read from the lower triangle, conjugated above the block) and P = C S with
+// S = A_kk^{-1} = X^H X, formed as P = (C X^H) X: thread (row i, column c) computes Y_ic = sum_{d<=c}
+// C_id conj(X_cd), then P_ic = sum_{d>=c} Y_id X_dc (c + 1 and bk - c terms: every thread does the
+// same work). Both go to column-major n x SB buffers: P for the update and the write-back, C as a
+// copy, because the update overwrites column and row k of A with P. The CTA over the pivot block's
+// rows also writes A_kk <- -S (lower triangle).
 constexpr int SP = 32;  // panel rows per CTA
-__global__ void __launch_bounds__(256) sweep_panel_kernel(const double2* __restrict__ w, int n, int k0, int bk,
+static_assert(SP == SB, "one panel CTA covers exactly the pivot block's rows");
+__global__ void __launch_bounds__(256) sweep_panel_kernel(double2* __restrict__ w, int n, int k0, int bk,
                                                           const double2* __restrict__ sbuf, double2* __restrict__ pbuf,
                                                           double2* __restrict__ cbuf) {
   const int l = blockIdx.y, i0 = blockIdx.x * SP, t = threadIdx.x;
-  const double2* m = w + (size_t)l * n * n;
+  double2* m = w + (size_t)l * n * n;
   __shared__ double2 cs[SP][SB + 1];
-  __shared__ double2 ss[SB][SB + 1];
+  __shared__ double2 xs[SB][SB + 1];
+  __shared__ double2 ys[SP][SB + 1];
   for (int e = t; e < SB * SB; e += blockDim.x) {
     const int i = e % SB, j = e / SB;
-    ss[i][j] = (i < bk && j < bk) ? sbuf[(size_t)l * SB * SB + j * SB + i] : make_double2(0.0, 0.0);
+    xs[i][j] = sbuf[(size_t)l * SB * SB + j * SB + i];  // zeros outside the bk x bk lower triangle
   }
   for (int e = t; e < SP * SB; e += blockDim.x) {  // rows at or below the block: lower triangle, i fastest
     const int r = e % SP, c = e / SP, i = i0 + r;
@@ -147,18 +147,40 @@ __global__ void __launch_bounds__(256) sweep_panel_kernel(const double2* __restr
   }
   __syncthreads();
   const int r = t % SP;
+  for (int c = t / SP; c < SB; c += 256 / SP) {  // Y = C X^H
+    double yr = 0.0, yi = 0.0;
+    for (int d = 0; d <= c; ++d) {  // C_rd conj(X_cd)
+      const double2 u = cs[r][d], v = xs[c][d];
+      yr = fma(u.x, v.x, fma(u.y, v.y, yr));
+      yi = fma(u.y, v.x, fma(-u.x, v.y, yi));
+    }
+    ys[r][c] = make_double2(yr, yi);
+  }
+  __syncthreads();
   const int i = i0 + r;
-  for (int c = t / SP; c < bk; c += 256 / SP) {
+  for (int c = t / SP; c < bk; c += 256 / SP) {  // P = Y X
     double pr = 0.0, pi = 0.0;
-#pragma unroll 8
-    for (int d = 0; d < SB; ++d) {
-      const double2 u = cs[r][d], v = ss[d][c];
+    for (int d = c; d < SB; ++d) {
+      const double2 u = ys[r][d], v = xs[d][c];
       pr = fma(u.x, v.x, fma(-u.y, v.y, pr));
       pi = fma(u.x, v.y, fma(u.y, v.x, pi));
     }
     if (i < n) {
       pbuf[((size_t)l * SB + c) * n + i] = make_double2(pr, pi);
       cbuf[((size_t)l * SB + c) * n + i] = cs[r][c];
+    }
+  }
+  if (i0 == k0) {  // A_kk <- -S, S = X^H X on the lower triangle
+    for (int e = t; e < bk * bk; e += blockDim.x) {
+      const int a = e % bk, b = e / bk;  // S(a, b), a >= b
+      if (a < b) continue;
+      double sr = 0.0, si = 0.0;
+      for (int c = a; c < bk; ++c) {  // conj(X_ca) X_cb
+        const double2 u = xs[c][a], v = xs[c][b];
+        sr = fma(u.x, v.x, fma(u.y, v.y, sr));
+        si = fma(u.x, v.y, fma(-u.y, v.x, si));
+      }
+      m[(size_t)(k0 + b) * n + k0 + a] = make_double2(-sr, a == b ? 0.0 : -si);
     }
   }
 }
@@ -489,8 +511,8 @@ void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, 
   for (int k0 = 0; k0 < n; k0 += SB) {
     const int bk = n - k0 < SB ? n - k0 : SB;
     sweep_pivot_kernel<<<L, 256, 0, s>>>(w, n, k0, bk, sbuf, d_info);
-    if (n <= bk) break;  // a single block: nothing outside it
     sweep_panel_kernel<<<dim3((n + SP - 1) / SP, L), 256, 0, s>>>(w, n, k0, bk, sbuf, pbuf, cbuf);
+    if (n <= bk) break;  // a single block: nothing outside it to update
     if (dig) {
       sweep_digits_kernel<<<dim3(nt, L, 2), 256, 0, s>>>(n, bk, pbuf, cbuf, imgA, imgB, eP, eC);
       sweep_update_tc_kernel<<<dim3(tiles, L), TC_THREADS, tc_update_smem(), s>>>(w, n, k0, bk, pbuf, imgA, imgB,
