@@ -47,6 +47,33 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
 
+// (hi 2^32 + lo) 2^sh as the nearest double (ties to even), in integer arithmetic: the 128-bit
+// value is exact, its leading 53 bits become the significand and the rest decides the rounding.
+// |hi| < 2^42, |lo| < 2^49; the result's exponent must stay in the normal range (the caller
+// bounds sh).
+__device__ __forceinline__ double i128_to_double(long long hi, long long lo, int sh) {
+  __int128 v = (__int128)hi * ((__int128)1 << 32) + lo;
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  unsigned __int128 m = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long mh0 = (unsigned long long)(m >> 64);
+  const int lz = mh0 ? __clzll((long long)mh0) : 64 + __clzll((long long)(unsigned long long)m);
+  m <<= lz;  // leading bit at 127
+  const unsigned long long mh = (unsigned long long)(m >> 64), ml = (unsigned long long)m;
+  unsigned long long mant = mh >> 11;  // 53 bits
+  const unsigned long long rem = mh & 0x7FFull;
+  const bool up = rem > 0x400ull || (rem == 0x400ull && (ml != 0 || (mant & 1ull)));
+  mant += up ? 1ull : 0ull;
+  int ex = 127 - lz + sh;  // exponent of the leading bit
+  if (mant >> 53) {
+    mant >>= 1;
+    ++ex;
+  }
+  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(ex + 1023) << 52) |
+                                  (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
 // One CTA per frequency: Cholesky of the pivot block A_kk = L L^H and X = L^{-1} (lower triangular,
 // written whole to sbuf[l], column-major SB x SB, zeros above the diagonal). The panel kernel forms
 // S = X^H X from it. info[l] keeps the first non-positive pivot (1-based global index); a failed
@@ -457,18 +484,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_update_tc_kernel(double2*
         const int J = tj * ST + c0 + jj;
         const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
         upd[jj] = I < n && J < n && I >= J && !inI && !inJ;
-        // the level sums are exact integers below 2^23: combine them exactly in two 64-bit words,
-        // hi = a0 2^16 + a1 2^8 + a2 and lo = a3 2^24 + a4 2^16 + a5 2^8 + a6, so that the value is
-        // (hi 2^-16 + lo 2^-48) 2^(-eP - eC), with two roundings in FP64
+        // the level sums are exact integers below 2^23: combine them exactly, hi = a0 2^16 + a1 2^8
+        // + a2 and lo = a3 2^24 + a4 2^16 + a5 2^8 + a6, value = (hi 2^32 + lo) 2^(-48 - eP - eC),
+        // rounded once to double in integer arithmetic (the FP64 pipe only does the subtraction)
         long long a[DL];
 #pragma unroll
         for (int lev = 0; lev < DL; ++lev) a[lev] = __float2int_rn(__uint_as_float(r[lev][jj]));
         const long long hi = a[0] * 65536LL + a[1] * 256LL + a[2];
         const long long lo = a[3] * 16777216LL + a[4] * 65536LL + a[5] * 256LL + a[6];
-        const int ee = e_i + sE[ST + c0 + jj];  // |ee| <= 800: both factors are normal doubles
-        const double c_hi = __longlong_as_double((long long)(1023 - 16 - ee) << 52);
-        const double c_lo = __longlong_as_double((long long)(1023 - 48 - ee) << 52);
-        val[jj] = fma((double)lo, c_lo, (double)hi * c_hi);
+        const int ee = e_i + sE[ST + c0 + jj];  // |ee| <= 800: the result stays a normal double
+        val[jj] = i128_to_double(hi, lo, -48 - ee);
       }
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj)  // the loads first, all independent
