@@ -241,19 +241,19 @@ struct PrepRowsArgs {
   int TJ, L, N;
 };
 
+// Row maxima of every chunk, zmax[c][I] = max over the chunk's columns of max(|Re z|, |Im z|), and
+// their exponents; grid (chunk, row tile < n_it, block).
 template <typename TZ>
-__global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ PrepRowsArgs p) {
+__global__ void __launch_bounds__(256) prep_max_kernel(const __grid_constant__ PrepRowsArgs p) {
   __shared__ float red[4][TI];
   const PrepRowsBlk& B = p.b[blockIdx.z];
   const int c = blockIdx.x, it = blockIdx.y;
-  if (c >= B.n_ch || it >= B.n_itb) return;
+  if (c >= B.n_ch || it >= B.n_it) return;
   const TZ* __restrict__ Z = static_cast<const TZ*>(B.Z);
   const long long ldz = B.ldz, K = B.K;
-  const int n_pb = B.n_pb, n_pad = B.n_pad, n_kb = B.n_kb, n_jt = B.n_jt, TJ = p.TJ, L = p.L, N = p.N;
-  const int BPLANE = 64 * N, BSTAGE = 3 * BPLANE;
   const int il = threadIdx.x & (TI - 1), q = threadIdx.x >> 6;
   const int I = it * TI + il;
-  const bool rowok = I < n_pb;
+  const bool rowok = I < B.n_pb;
   float m = 0.f;
   for (int jc = q; jc < CHR; jc += 4) {
     const long long r = (long long)c * CHR + jc;
@@ -264,32 +264,66 @@ __global__ void __launch_bounds__(256) prep_rows_kernel(const __grid_constant__ 
   }
   red[q][il] = m;
   __syncthreads();
-  m = fmaxf(fmaxf(red[0][il], red[1][il]), fmaxf(red[2][il], red[3][il]));
-  const int eA = scale_exp(m);
-  if (q == 0 && I < n_pad) {
-    B.zmax[(size_t)c * n_pad + I] = m;
-    B.expA[(size_t)c * n_pad + I] = eA;
+  if (q == 0) {
+    m = fmaxf(fmaxf(red[0][il], red[1][il]), fmaxf(red[2][il], red[3][il]));
+    B.zmax[(size_t)c * B.n_pad + I] = m;
+    B.expA[(size_t)c * B.n_pad + I] = scale_exp(m);
   }
-  const float sA = exp2i(eA);
+}
+
+// The digit planes: PR_SPLIT CTAs per (chunk, row tile), each over KB_PER_CH / PR_SPLIT K-blocks, so
+// the grid fills the SMs in several waves; the row maxima come from prep_max_kernel.
+constexpr int PR_SPLIT = 8;
+template <typename TZ>
+__global__ void __launch_bounds__(256, 3) prep_rows_kernel(const __grid_constant__ PrepRowsArgs p) {
+  const PrepRowsBlk& B = p.b[blockIdx.z];
+  const int c = blockIdx.x / PR_SPLIT, part = blockIdx.x % PR_SPLIT, it = blockIdx.y;
+  if (c >= B.n_ch || it >= B.n_itb) return;
+  const TZ* __restrict__ Z = static_cast<const TZ*>(B.Z);
+  const long long ldz = B.ldz, K = B.K;
+  const int n_pb = B.n_pb, n_pad = B.n_pad, n_kb = B.n_kb, n_jt = B.n_jt, TJ = p.TJ, L = p.L, N = p.N;
+  const int BPLANE = 64 * N, BSTAGE = 3 * BPLANE;
+  const int il = threadIdx.x & (TI - 1), q = threadIdx.x >> 6;
+  const int I = it * TI + il;
+  const bool rowok = I < n_pb;
   const int jt = I / TJ, jj = I % TJ;
   const bool need_b = jt < n_jt && I >= B.b_row0;
   // CTA-uniform: b_row0 is a multiple of the tile rows, and tiles past n_it carry B rows only
   const bool need_a = it < B.n_it && it * TI < B.a_rows;
   if (!need_a && !(it * TI + TI > B.b_row0 && it * TI < n_jt * TJ)) return;
+  const float m = rowok ? B.zmax[(size_t)c * n_pad + I] : 0.f;  // rows past n_pb: zero
+  const float sA = exp2i(scale_exp(m));
   float bsc[kMaxOmega];  // 2^eB of this column for every frequency (the kernel's epilogue uses 2^-eB)
 #pragma unroll
   for (int l = 0; l < kMaxOmega; ++l)
     bsc[l] = l < L ? exp2i(scale_exp(B.wmax[(size_t)c * L + l] * m)) : 0.f;
-  for (int kbl = 0; kbl < KB_PER_CH; ++kbl) {
-    const int kb = c * KB_PER_CH + kbl;
+  const int kb_begin = c * KB_PER_CH + part * (KB_PER_CH / PR_SPLIT);
+  float na[4], nb[4];  // the next K-block's values, loaded one step ahead
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const long long r = (long long)kb_begin * KBR + q * 4 + rr;
+    TZ z{};
+    if (rowok && r < K) z = Z[I + r * ldz];
+    na[rr] = (float)z.x;
+    nb[rr] = (float)z.y;
+  }
+  for (int kbi = 0; kbi < KB_PER_CH / PR_SPLIT; ++kbi) {
+    const int kb = kb_begin + kbi;
     float a[4], b[4];
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
-      const long long r = (long long)kb * KBR + q * 4 + rr;
-      TZ z{};
-      if (rowok && r < K) z = Z[I + r * ldz];
-      a[rr] = (float)z.x;
-      b[rr] = (float)z.y;
+      a[rr] = na[rr];
+      b[rr] = nb[rr];
+    }
+    if (kbi + 1 < KB_PER_CH / PR_SPLIT) {
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const long long r = (long long)(kb + 1) * KBR + q * 4 + rr;
+        TZ z{};
+        if (rowok && r < K) z = Z[I + r * ldz];
+        na[rr] = (float)z.x;
+        nb[rr] = (float)z.y;
+      }
     }
     if (need_a) {
       float da[3][4], db[3][4];
@@ -990,7 +1024,7 @@ static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* 
     pr[t].N = N;
   }
   int T = 0, min_ch_tail = 1 << 30;
-  int nr[2] = {0, 0}, max_it[2] = {0, 0}, max_chr[2] = {0, 0}, max_ch = 0;
+  int nr[2] = {0, 0}, max_it[2] = {0, 0}, max_ita[2] = {0, 0}, max_chr[2] = {0, 0}, max_ch = 0;
   for (int b = 0; b < nb; ++b) {
     const MixedBlock& B = in[b];
     BlockDesc& d = a.blk[b];
@@ -1018,10 +1052,17 @@ static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* 
     max_ch = std::max(max_ch, G[b].n_ch);
     max_chr[t] = std::max(max_chr[t], G[b].n_ch);
     max_it[t] = std::max(max_it[t], G[b].n_itb);
+    max_ita[t] = std::max(max_ita[t], G[b].n_it);
   }
   prep_cols_kernel<<<dim3(max_ch, nb), PC_THREADS, 0, stream>>>(pc);
-  if (nr[0] > 0) prep_rows_kernel<double2><<<dim3(max_chr[0], max_it[0], nr[0]), 256, 0, stream>>>(pr[0]);
-  if (nr[1] > 0) prep_rows_kernel<float2><<<dim3(max_chr[1], max_it[1], nr[1]), 256, 0, stream>>>(pr[1]);
+  if (nr[0] > 0) {
+    prep_max_kernel<double2><<<dim3(max_chr[0], max_ita[0], nr[0]), 256, 0, stream>>>(pr[0]);
+    prep_rows_kernel<double2><<<dim3(max_chr[0] * PR_SPLIT, max_it[0], nr[0]), 256, 0, stream>>>(pr[0]);
+  }
+  if (nr[1] > 0) {
+    prep_max_kernel<float2><<<dim3(max_chr[1], max_ita[1], nr[1]), 256, 0, stream>>>(pr[1]);
+    prep_rows_kernel<float2><<<dim3(max_chr[1] * PR_SPLIT, max_it[1], nr[1]), 256, 0, stream>>>(pr[1]);
+  }
   // whole tiles first; the last R tiles (a partial last wave) are split into P chunk ranges
   const int Gc = grid_cap;
   const int R = T >= Gc ? T % Gc : T;
