@@ -31,10 +31,11 @@
 // run; GB300's FP64 rate (~1.2 TFLOP/s) would make an FP64 read-modify-write here the bottleneck.
 //
 // Both operands' digits are formed once per call by the row preparation, as the exact
-// shared-memory image of each K-block: the A planes per 64-row I tile, the B planes (all
-// frequencies, scaled) per J tile. Every output tile of a J tile column reads the same B image, so
-// forming B in each CTA repeated the same digit arithmetic once per I tile; now the tensor-core
-// kernel only moves both images with bulk copies and issues the MMAs.
+// shared-memory image of each K-block: the Re rows (a, b) of every row (the row image), and the
+// B planes (all frequencies, scaled) per J tile. Every output tile of a J tile column reads the same
+// B image, so forming B in each CTA repeated the same digit arithmetic once per I tile; the
+// tensor-core kernel moves the images with bulk copies, forms the Im rows (-b, a) of A in shared
+// memory and issues the MMAs. At one frequency (L = 1) the row image is the B operand as well.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -53,6 +54,7 @@ constexpr float DMAX = 90.f;              // |leading digit| bound: 2 * CHR * DM
 constexpr int KB_PER_CH = CHR / KBR;      // 64
 constexpr int TI = 64;                    // rows I per tile (M = 128)
 constexpr int A_PLANE = 128 * KBK * 2;    // bytes of one digit plane of one A K-block (8 KB)
+constexpr int A_HALF = A_PLANE / 2;       // its 64 Re rows (4 KB); the 64 Im rows follow
 constexpr int A_STAGE = 3 * A_PLANE;      // 24 KB
 constexpr int NS = 3;                     // pipeline stages: the A and B digit planes of one K-block each
 constexpr size_t kSmemMax = 227 * 1024;
@@ -211,38 +213,51 @@ __global__ void __launch_bounds__(PC_THREADS) prep_cols_kernel(const __grid_cons
 }
 
 // ------------------------------------------------------------------ prep: rows
-// One CTA per (chunk, 64-row tile): chunk maximum of max(|Re z|, |Im z|) per row, its exponent,
-// the A-operand digit planes of the row tile and the B-operand digit planes of the rows' J columns,
-// both written as the exact shared-memory image of each K-block (canonical no-swizzle K-major:
-// 16-byte rows of 8 K' values, 8-row core matrices 128 bytes apart), so the tensor-core kernel moves
-// each K-block with one bulk copy per operand.
-//   A image [plane][k-group 4][row-group 16][8 rows][8 K'] (rows: 64 Re rows (a, b), 64 Im rows (-b, a));
-//   B image of J tile jt [plane][k-group 4][n-group N/8][8 n][8 K'], n = l * TJ + j, values
-//     2^eB w_l(Delta_r) z_{J, r} (re, im pairs along K'), eB from max_r |w_l| * max_r |z_J| of the chunk.
+// Shared-memory operand layout (both operands, canonical no-swizzle K-major): 8-row core matrices of
+// 16-byte rows (8 K' values), the 4 core matrices of a row group along K' 128 bytes apart, row
+// groups 512 bytes apart; one digit plane of R rows of a K-block is R * 64 bytes:
+//   byte (row >> 3) * 512 + kgroup * 128 + (row & 7) * 16.
+// Row image (A operand, and at L = 1 also the B operand): for every K-block and digit plane, the
+// (a, b) digit pairs of all prep rows in that layout, [K-block][plane][n_rows * 64 bytes], so the 64
+// rows of an I tile (or the TJ rows of a J tile) are one contiguous slice. The tensor-core kernel
+// copies an I tile's slice into the 64 Re rows of its A stage and forms the 64 Im rows (-b, a) from
+// them in shared memory, so the imaginary rows never travel through HBM.
+// B image of J tile jt (L >= 2): [K-block][plane][n = l * TJ + j in the same layout], values
+// 2^eB w_l(Delta_r) z_{J, r} (re, im pairs along K'), eB from max_r |w_l| * max_r |z_J| of the chunk.
 // Every CTA of a J tile column, and every I tile, reads the same B image, so the scaled digits of a
-// column are formed once per call rather than once per output tile. Rows past n_pad (J tiles reach
-// n_jt * TJ) get zero B digits. TZ: double2 (complex128 input) or float2 (complex64): every element
-// is rounded to FP32 on load. All blocks of one launch have the same TZ; grid (chunk, row tile,
-// block), CTAs past a block's chunk or row-tile count leave at once.
+// column are formed once per call rather than once per output tile.
+// At L = 1 the weights are positive and the product conj(z_I) w z_J is the product of the rows
+// y = sqrt(w) z of both sides, so one row image with per-row exponents serves both operands: its
+// digits are those of the exact product (FP32 sqrt(w)) (FP32 z) scaled by 2^e_I, e_I from the chunk
+// maximum of |y_I|, and the epilogue takes 2^-(e_I + e_J) off each element.
+// Rows past n_pb get zero digits. TZ: double2 (complex128 input) or float2 (complex64): every
+// element is rounded to FP32 on load. All blocks of one launch have the same TZ.
 struct PrepRowsBlk {
   const void* Z;  // TZ [r][ldz], at the launch's first column
   long long ldz, K;
-  uint8_t* aplanes;
-  uint8_t* bplanes;
+  uint8_t* rimg;      // row image [n_kb][3][n_rows * 64]
+  uint8_t* bplanes;   // B image [n_jt][n_kb][3][N * 64] (L >= 2)
   const float* wst;   // [r][L] weights (prep_cols)
   const float* wmax;  // [chunk][L] their chunk maxima
   float* zmax;
   int* expA;
   int n_pb, n_pad, n_kb, n_jt, n_ch, n_it, n_itb;
-  int a_rows, b_row0;  // rows I < a_rows need row digit planes, rows I >= b_row0 column digit planes
+  int a_rows;  // rows I < a_rows are A rows (all rows, or the first row set of a restricted block)
+  int b_row0;  // rows I >= b_row0 are B rows (0, or the restricted block's col0)
 };
 struct PrepRowsArgs {
   PrepRowsBlk b[kMaxBlocks];
   int TJ, L, N;
 };
 
-// Row maxima of every chunk, zmax[c][I] = max over the chunk's columns of max(|Re z|, |Im z|), and
-// their exponents; grid (chunk, row tile < n_it, block).
+// The row value that enters the digits: z itself, or sqrt(w_r) z at L = 1.
+__device__ __forceinline__ float row_weight(const float* wst, long long r, int L) {
+  return L == 1 ? sqrtf(wst[r]) : 1.f;
+}
+
+// Row maxima of every chunk, zmax[c][I] = max over the chunk's columns of max(|Re y|, |Im y|) (y the
+// row value above, each |.| the FP32 product), and their exponents; grid (chunk, row tile < n_it,
+// block).
 template <typename TZ>
 __global__ void __launch_bounds__(256) prep_max_kernel(const __grid_constant__ PrepRowsArgs p) {
   __shared__ float red[4][TI];
@@ -259,7 +274,8 @@ __global__ void __launch_bounds__(256) prep_max_kernel(const __grid_constant__ P
     const long long r = (long long)c * CHR + jc;
     if (rowok && r < K) {
       const TZ z = Z[I + r * ldz];
-      m = fmaxf(m, fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
+      const float s = row_weight(B.wst, r, p.L);
+      m = fmaxf(m, s * fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
     }
   }
   red[q][il] = m;
@@ -271,8 +287,9 @@ __global__ void __launch_bounds__(256) prep_max_kernel(const __grid_constant__ P
   }
 }
 
-// The digit planes: PR_SPLIT CTAs per (chunk, row tile), each over KB_PER_CH / PR_SPLIT K-blocks, so
-// the grid fills the SMs in several waves; the row maxima come from prep_max_kernel.
+// The digit planes: PR_SPLIT CTAs per (chunk, 64-row tile), each over KB_PER_CH / PR_SPLIT K-blocks,
+// so the grid fills the SMs in several waves; the row maxima come from prep_max_kernel. Thread
+// (row il, k-group q) forms the digits of 4 columns of its row per K-block.
 constexpr int PR_SPLIT = 8;
 template <typename TZ>
 __global__ void __launch_bounds__(256, 3) prep_rows_kernel(const __grid_constant__ PrepRowsArgs p) {
@@ -282,21 +299,25 @@ __global__ void __launch_bounds__(256, 3) prep_rows_kernel(const __grid_constant
   const TZ* __restrict__ Z = static_cast<const TZ*>(B.Z);
   const long long ldz = B.ldz, K = B.K;
   const int n_pb = B.n_pb, n_pad = B.n_pad, n_kb = B.n_kb, n_jt = B.n_jt, TJ = p.TJ, L = p.L, N = p.N;
+  const size_t RPLANE = (size_t)B.n_itb * TI * 64;  // bytes of one plane of the row image per K-block
   const int BPLANE = 64 * N, BSTAGE = 3 * BPLANE;
   const int il = threadIdx.x & (TI - 1), q = threadIdx.x >> 6;
   const int I = it * TI + il;
   const bool rowok = I < n_pb;
   const int jt = I / TJ, jj = I % TJ;
-  const bool need_b = jt < n_jt && I >= B.b_row0;
+  const bool sym = L == 1;
   // CTA-uniform: b_row0 is a multiple of the tile rows, and tiles past n_it carry B rows only
   const bool need_a = it < B.n_it && it * TI < B.a_rows;
   if (!need_a && !(it * TI + TI > B.b_row0 && it * TI < n_jt * TJ)) return;
+  const bool need_b = jt < n_jt && I >= B.b_row0;
+  const bool need_row = need_a || (sym && need_b);  // this row's slice of the row image is read
   const float m = rowok ? B.zmax[(size_t)c * n_pad + I] : 0.f;  // rows past n_pb: zero
   const float sA = exp2i(scale_exp(m));
   float bsc[kMaxOmega];  // 2^eB of this column for every frequency (the kernel's epilogue uses 2^-eB)
 #pragma unroll
   for (int l = 0; l < kMaxOmega; ++l)
     bsc[l] = l < L ? exp2i(scale_exp(B.wmax[(size_t)c * L + l] * m)) : 0.f;
+  const int rofs = (I >> 3) * 512 + q * 128 + (I & 7) * 16;  // this thread's 16 bytes in a row-image plane
   const int kb_begin = c * KB_PER_CH + part * (KB_PER_CH / PR_SPLIT);
   float na[4], nb[4];  // the next K-block's values, loaded one step ahead
 #pragma unroll
@@ -325,33 +346,37 @@ __global__ void __launch_bounds__(256, 3) prep_rows_kernel(const __grid_constant
         nb[rr] = (float)z.y;
       }
     }
-    if (need_a) {
+    if (need_row) {
       float da[3][4], db[3][4];
+      if (sym) {  // digits of the exact products (sqrt(w_r) 2^e) a and (sqrt(w_r) 2^e) b
+        const float* wr = B.wst + (size_t)kb * KBR + q * 4;
 #pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        digits3(a[rr] * sA, da[0][rr], da[1][rr], da[2][rr]);
-        digits3(b[rr] * sA, db[0][rr], db[1][rr], db[2][rr]);
+        for (int rr = 0; rr < 4; ++rr) {
+          const float ws = sqrtf(wr[rr]) * sA;
+          digits3_mul(ws, a[rr], da[0][rr], da[1][rr], da[2][rr]);
+          digits3_mul(ws, b[rr], db[0][rr], db[1][rr], db[2][rr]);
+        }
+      } else {
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          digits3(a[rr] * sA, da[0][rr], da[1][rr], da[2][rr]);
+          digits3(b[rr] * sA, db[0][rr], db[1][rr], db[2][rr]);
+        }
       }
-      uint8_t* base = B.aplanes + ((size_t)it * n_kb + kb) * A_STAGE + q * 2048;
+      uint8_t* base = B.rimg + (size_t)kb * 3 * RPLANE + rofs;
 #pragma unroll
       for (int pl = 0; pl < 3; ++pl) {
-        uint4 re, im;  // Re row: (a, b) pairs; Im row: (-b, a) pairs
+        uint4 re;  // (a, b) pairs along K'
         re.x = pack_h2(da[pl][0], db[pl][0]);
         re.y = pack_h2(da[pl][1], db[pl][1]);
         re.z = pack_h2(da[pl][2], db[pl][2]);
         re.w = pack_h2(da[pl][3], db[pl][3]);
-        im.x = pack_h2(-db[pl][0], da[pl][0]);
-        im.y = pack_h2(-db[pl][1], da[pl][1]);
-        im.z = pack_h2(-db[pl][2], da[pl][2]);
-        im.w = pack_h2(-db[pl][3], da[pl][3]);
-        const int mre = il, mim = TI + il;
-        *reinterpret_cast<uint4*>(base + pl * A_PLANE + (mre >> 3) * 128 + (mre & 7) * 16) = re;
-        *reinterpret_cast<uint4*>(base + pl * A_PLANE + (mim >> 3) * 128 + (mim & 7) * 16) = im;
+        *reinterpret_cast<uint4*>(base + pl * RPLANE) = re;
       }
     }
-    if (need_b) {
+    if (need_b && !sym) {
       const float* wr = B.wst + ((size_t)kb * KBR + q * 4) * L;  // this thread's 4 columns, every frequency
-      uint8_t* bb = B.bplanes + ((size_t)jt * n_kb + kb) * BSTAGE + q * 16 * N;
+      uint8_t* bb = B.bplanes + ((size_t)jt * n_kb + kb) * BSTAGE + q * 128;
 #pragma unroll
       for (int l = 0; l < kMaxOmega; ++l) {  // to the constant bound, so bsc stays in registers
         if (l >= L) break;
@@ -363,7 +388,7 @@ __global__ void __launch_bounds__(256, 3) prep_rows_kernel(const __grid_constant
           digits3_mul(ww, b[rr], d[0][2 * rr + 1], d[1][2 * rr + 1], d[2][2 * rr + 1]);
         }
         const int n = l * TJ + jj;
-        uint8_t* dst = bb + (n >> 3) * 128 + (n & 7) * 16;
+        uint8_t* dst = bb + (n >> 3) * 512 + (n & 7) * 16;
 #pragma unroll
         for (int pl = 0; pl < 3; ++pl) {
           uint4 v;
@@ -381,8 +406,8 @@ __global__ void __launch_bounds__(256, 3) prep_rows_kernel(const __grid_constant
 // ------------------------------------------------------------------ main tensor-core kernel
 // One block of transition columns (one accumulate request) for one q-point, as the kernel sees it.
 struct BlockDesc {
-  const uint8_t* aplanes;
-  const uint8_t* bplanes;
+  const uint8_t* rimg;     // row image [n_kb][3][n_rows * 64]
+  const uint8_t* bplanes;  // B image (L >= 2)
   const float* zmax;
   const int* expA;
   const float* wmax;
@@ -392,6 +417,7 @@ struct BlockDesc {
   int tile_off;   // first global tile index of this block
   int n_pb, n_pad, n_kb, n_tiles, n_ch;
   int n_kbr;      // K-blocks holding columns (ceil(K / KBR)); the rest of the last chunk is padding
+  int n_rows;     // rows of the row image (a multiple of 64)
 };
 constexpr int kFscrPerCta = 256 * 128;  // flush scratch pairs per CTA: [column n < 256][accumulator lane < 128]
 
@@ -500,7 +526,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
   uint64_t* finbar = accempty + 1;
   uint64_t* stashed = finbar + 1;    // 8 epilogue warps -> drainers: a chunk end (stash or heartbeat)
   uint64_t* drained = stashed + 1;   // 2 drainer warps -> epilogue: that stash is in the accumulator
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
+  uint64_t* built = drained + 1;     // [NS]   8 epilogue warps -> MMA: the stage's Im rows are formed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(built + NS);
   int* abortB = reinterpret_cast<int*>(tmem_slot + 1);  // [2] epilogue-warp failure flags, by chunk parity
   int* sdesc = abortB + 2;  // [8] stash: kind (1 whole-tile chunk, 3 piece chunk, 2 end), block, it, jt, chunk,
                             //     parity, piece, first chunk of the piece
@@ -514,6 +541,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1 + NBG / 32);
+      mbar_init(&built[s], NBG / 32);
     }
     mbar_init(accfull, 1);
     mbar_init(accempty, NBG / 32);
@@ -558,9 +586,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             break;
           }
           uint8_t* st = sStage + s * STAGE;
-          mbar_arrive_expect_tx(&full[s], STAGE);
-          bulk_g2s(st, bd.aplanes + ((size_t)tile.x * bd.n_kb + kb) * A_STAGE, A_STAGE, &full[s]);
-          bulk_g2s(st + A_STAGE, bd.bplanes + ((size_t)tile.y * bd.n_kb + kb) * BSTAGE, BSTAGE, &full[s]);
+          const size_t rplane = (size_t)bd.n_rows * 64;
+          const uint8_t* rk = bd.rimg + (size_t)kb * 3 * rplane;
+          mbar_arrive_expect_tx(&full[s], 3 * A_HALF + BSTAGE);
+          for (int pl = 0; pl < 3; ++pl)  // the I tile's 64 Re rows of each plane
+            bulk_g2s(st + pl * A_PLANE, rk + pl * rplane + (size_t)tile.x * TI * 64, A_HALF, &full[s]);
+          if (L == 1) {  // the J tile's TJ rows of the same row image
+            for (int pl = 0; pl < 3; ++pl)
+              bulk_g2s(st + A_STAGE + pl * BPLANE, rk + pl * rplane + (size_t)tile.y * TJ * 64, BPLANE, &full[s]);
+          } else {
+            bulk_g2s(st + A_STAGE, bd.bplanes + ((size_t)tile.y * bd.n_kb + kb) * BSTAGE, BSTAGE, &full[s]);
+          }
           issued = g + 1;
         }
         if (stop || (cur.flags & 1)) break;
@@ -587,7 +623,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         int nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
         for (int kbi = 0; kbi < nkb; ++kbi, ++g) {
           const int s = g % NS, kbl = kbi % KB_PER_CH;
-          bool ok = mbar_wait_bounded(&full[s], (g / NS) & 1, kWaitNs);
+          bool ok = mbar_wait_bounded(&built[s], (g / NS) & 1, kWaitNs);
           if (ok && kbi == 0 && pos > 0) {  // the item was published before this K-block's copies
             cur = ring[pos % kRing];
             nkb = item_nkb(cur, sBlk[block_of_tile(sBlk, p.nb, cur.gt)]);
@@ -602,14 +638,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           tc_fence_after();
           const uint32_t a_base = smem_u32(sStage + s * STAGE), b_base = a_base + A_STAGE;
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t ao = a_base + ks * 4096, bo = b_base + ks * 32 * N;
-            const uint64_t a0 = make_smem_desc(ao, 2048, 128, 0);
-            const uint64_t a1 = make_smem_desc(ao + A_PLANE, 2048, 128, 0);
-            const uint64_t a2 = make_smem_desc(ao + 2 * A_PLANE, 2048, 128, 0);
-            const uint64_t b0 = make_smem_desc(bo, 16 * N, 128, 0);
-            const uint64_t b1 = make_smem_desc(bo + BPLANE, 16 * N, 128, 0);
-            const uint64_t b2 = make_smem_desc(bo + 2 * BPLANE, 16 * N, 128, 0);
+          for (int ks = 0; ks < 2; ++ks) {  // k-groups 2 ks, 2 ks + 1: 128 bytes apart, row groups 512
+            const uint32_t ao = a_base + ks * 256, bo = b_base + ks * 256;
+            const uint64_t a0 = make_smem_desc(ao, 128, 512, 0);
+            const uint64_t a1 = make_smem_desc(ao + A_PLANE, 128, 512, 0);
+            const uint64_t a2 = make_smem_desc(ao + 2 * A_PLANE, 128, 512, 0);
+            const uint64_t b0 = make_smem_desc(bo, 128, 512, 0);
+            const uint64_t b1 = make_smem_desc(bo + BPLANE, 128, 512, 0);
+            const uint64_t b2 = make_smem_desc(bo + 2 * BPLANE, 128, 512, 0);
             const uint32_t acc_in = (kbl == 0 && ks == 0) ? 0u : 1u;
             mma_f16(tmem, a0, b0, idesc, acc_in);
             mma_f16(tmem + TMEM_L12, a0, b1, idesc, acc_in);
@@ -629,9 +665,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
       mbar_wait_bounded(finbar, 0, kWaitNs);
     }
   } else if (warp < 2 + NBG / 32) {
-    // ---------------- epilogue warps: the chunk's B scales for the drainers + the chunk epilogue.
-    // They follow the K-blocks (wait on full, arrive on empty) only to read the item ring in step
-    // with the producer and to keep the stages' phases from running ahead of them.
+    // ---------------- epilogue warps: the Im rows of each A stage, the chunk's B scales for the
+    // drainers, and the chunk epilogue. Per K-block they wait for the copies, form the 64 Im rows
+    // (-b, a) of every plane from the 64 Re rows (a, b) (swap the FP16 halves of each pair, flip the
+    // sign of the new low half), hand the stage to the MMA issuer and release it to the producer.
     const int bt = tid - 64;
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
     const int wg = (warp - 2) >> 2;           // column half handled in the epilogue
@@ -676,12 +713,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
           it = tile.x;
           jt = tile.y;
         }
+        if (!dead) {
+          uint4* st4 = reinterpret_cast<uint4*>(sStage + s * STAGE);
+#pragma unroll
+          for (int pl = 0; pl < 3; ++pl) {
+            uint4 v = st4[pl * (A_PLANE / 16) + bt];
+            v.x = __byte_perm(v.x, 0, 0x1032) ^ 0x8000u;
+            v.y = __byte_perm(v.y, 0, 0x1032) ^ 0x8000u;
+            v.z = __byte_perm(v.z, 0, 0x1032) ^ 0x8000u;
+            v.w = __byte_perm(v.w, 0, 0x1032) ^ 0x8000u;
+            st4[pl * (A_PLANE / 16) + A_HALF / 16 + bt] = v;
+          }
+          fence_proxy_async_smem();  // visible to the tensor core's reads
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&built[s]);
+        }
         const BlockDesc& bd = sBlk[b];
         const int c = cur.c0 + kbi / KB_PER_CH;
         if (kbl == 0 && has_col) {  // 2^-eB of this chunk, the inverse of the scale the prep applied
           const int J = jt * TJ + bj;
-          const float zm = J < bd.n_pb ? bd.zmax[(size_t)c * bd.n_pad + J] : 0.f;
-          sScB[(lc & 1) * 256 + bt] = exp2i(-scale_exp(bd.wmax[c * L + bl] * zm));
+          if (L == 1) {
+            sScB[(lc & 1) * 256 + bt] = J < bd.n_pb ? exp2i(-bd.expA[(size_t)c * bd.n_pad + J]) : 0.f;
+          } else {
+            const float zm = J < bd.n_pb ? bd.zmax[(size_t)c * bd.n_pad + J] : 0.f;
+            sScB[(lc & 1) * 256 + bt] = exp2i(-scale_exp(bd.wmax[c * L + bl] * zm));
+          }
         }
         __syncwarp();
         if (lane == 0 && !dead) mbar_arrive(&empty[s]);
@@ -962,14 +1018,20 @@ static Geom geom_of(int n_pb, int n_pad, long long K, int TJ) {
   G.n_itb = (std::max(n_pad, G.n_jt * TJ) + TI - 1) / TI;  // row tiles of the prep: A rows and B rows
   return G;
 }
+// Digit-plane bytes of one K-block: the row image, and the B image unless L = 1 (where the row
+// image is the B operand too).
+static size_t plane_bytes_per_kb(const Geom& G, int N, int L) {
+  return (size_t)3 * G.n_itb * TI * 64 + (L == 1 ? 0 : (size_t)G.n_jt * b_stage_bytes(N));
+}
 static size_t geom_bytes(const Geom& G, int n_pad, int N, int L) {
-  return align256((size_t)G.n_it * G.n_kb * A_STAGE) + align256((size_t)G.n_jt * G.n_kb * b_stage_bytes(N)) +
+  return align256((size_t)G.n_kb * 3 * G.n_itb * TI * 64) +
+         align256(L == 1 ? 0 : (size_t)G.n_jt * G.n_kb * b_stage_bytes(N)) +
          align256((size_t)G.n_kb * KBR * L * sizeof(float)) + 2 * align256((size_t)G.n_ch * n_pad * sizeof(float)) +
          align256((size_t)G.n_ch * L * sizeof(float));
 }
 struct Carve {
-  uint8_t* a;
-  uint8_t* b;
+  uint8_t* a;  // row image
+  uint8_t* b;  // B image (null at L = 1)
   float* w;
   float* zmax;
   int* expA;
@@ -979,9 +1041,9 @@ static Carve carve(uint8_t* base, const Geom& G, int n_pad, int N, int L) {
   Carve c;
   size_t o = 0;
   c.a = base + o;
-  o += align256((size_t)G.n_it * G.n_kb * A_STAGE);
-  c.b = base + o;
-  o += align256((size_t)G.n_jt * G.n_kb * b_stage_bytes(N));
+  o += align256((size_t)G.n_kb * 3 * G.n_itb * TI * 64);
+  c.b = L == 1 ? nullptr : base + o;
+  o += align256(L == 1 ? 0 : (size_t)G.n_jt * G.n_kb * b_stage_bytes(N));
   c.w = reinterpret_cast<float*>(base + o);
   o += align256((size_t)G.n_kb * KBR * L * sizeof(float));
   c.zmax = reinterpret_cast<float*>(base + o);
@@ -1028,7 +1090,7 @@ static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* 
   for (int b = 0; b < nb; ++b) {
     const MixedBlock& B = in[b];
     BlockDesc& d = a.blk[b];
-    d.aplanes = S[b].a;
+    d.rimg = S[b].a;
     d.bplanes = S[b].b;
     d.zmax = S[b].zmax;
     d.expA = S[b].expA;
@@ -1043,6 +1105,7 @@ static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* 
     d.n_kb = G[b].n_kb;
     d.n_kbr = (int)((G[b].K + KBR - 1) / KBR);
     d.n_ch = G[b].n_ch;
+    d.n_rows = G[b].n_itb * TI;
     T += d.n_tiles;
     pc.b[b] = PrepColsBlk{B.eo, B.eu, B.wv, S[b].w, S[b].wmax, G[b].K, r0[b], B.n_unocc, G[b].n_ch};
     const int t = B.z32 ? 1 : 0;
@@ -1085,8 +1148,8 @@ static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* 
   return cudaGetLastError() == cudaSuccess ? QSGW_OK : QSGW_ERR_CUDA;
 }
 
-// B digit planes of one launch at most: a call whose planes would exceed it runs as launches over
-// chunk ranges (every launch covers the same chunks of every block; each chunk is flushed into the
+// Digit planes (row image and B image) of one launch at most: a call whose planes would exceed it
+// runs as launches over chunk ranges (every launch covers the same chunks of every block; each chunk is flushed into the
 // accumulator anyway, so the cut changes nothing but the launch count).
 constexpr size_t kBPlaneBudget = 8ull << 30;
 
@@ -1129,7 +1192,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
   int n_tiles[kMaxBlocks];
   long long Kb[kMaxBlocks];
   int max_ch = 0;
-  size_t b_per_chunk = 0;  // B digit-plane bytes of one chunk of every block
+  size_t b_per_chunk = 0;  // digit-plane bytes of one chunk of every block
   for (int b = 0; b < nb; ++b) {
     const MixedBlock& B = in[b];
     if (B.rows_i > 0 && (B.col0 % TJ != 0 || B.col0 < B.rows_i || B.col0 >= B.n_pb)) return QSGW_ERR_ARG;
@@ -1137,7 +1200,7 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
     if (st != QSGW_OK) return st;
     Kb[b] = (long long)B.n_occ * B.n_unocc;
     max_ch = std::max(max_ch, (int)((Kb[b] + CHR - 1) / CHR));
-    b_per_chunk += (size_t)((B.n_pb + TJ - 1) / TJ) * KB_PER_CH * b_stage_bytes(N);
+    b_per_chunk += KB_PER_CH * plane_bytes_per_kb(geom_of(B.n_pb, B.n_pad, CHR, TJ), N, L);
   }
   int cpl = max_ch;  // chunks per launch
   if ((size_t)cpl * b_per_chunk > kBPlaneBudget) cpl = std::max(1, (int)(kBPlaneBudget / b_per_chunk));
