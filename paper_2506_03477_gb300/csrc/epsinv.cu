@@ -93,17 +93,18 @@ __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ 
   }
   __syncthreads();
   for (int j = 0; j < bk; ++j) {  // right-looking Cholesky of the block
-    double d = a[j][j].x;
-    if (!(d > 0.0)) {
-      if (t == 0 && fail == 0) fail = j + 1;
-      d = 1.0;
-    }
-    const double r = sqrt(d), ri = 1.0 / r;
-    __syncthreads();  // every thread has read the pivot
-    if (t == 0) {
+    if (t == 0) {  // one thread: an FP64 square root and division cost dozens of FP64 operations
+      double d = a[j][j].x;
+      if (!(d > 0.0)) {
+        if (fail == 0) fail = j + 1;
+        d = 1.0;
+      }
+      const double r = sqrt(d);
       a[j][j] = make_double2(r, 0.0);
-      rdiag[j] = ri;
+      rdiag[j] = 1.0 / r;
     }
+    __syncthreads();
+    const double ri = rdiag[j];
     for (int i = j + 1 + t; i < bk; i += blockDim.x) {
       a[i][j].x *= ri;
       a[i][j].y *= ri;

@@ -25,10 +25,11 @@
 // on a narrow block, above the 1e-6 bar, against ~0.4e-6 at 1024. With |d1| <= 1/2 and |d2| <=
 // 2^-12 the dropped products d1 d2, d2 d1 and d2 d2 are below 2^-13 each, ~2^-26 of the largest
 // product 90^2, under the FP32 rounding of the inputs; so 6 MMA products serve a flop pair (BF16
-// digits, 8 significant bits, left d1 d2 at ~2^-20 and needed 8). After each chunk
-// both accumulators are stashed, and two drainer warps scale them by 2^-(eA+eB) (exact) and add
-// them into a double-float (2 x FP32) accumulator in global memory while the next chunk's MMAs
-// run; GB300's FP64 rate (~1.2 TFLOP/s) would make an FP64 read-modify-write here the bottleneck.
+// digits, 8 significant bits, left d1 d2 at ~2^-20 and needed 8). After each chunk the sum of
+// both accumulators, rounded once to FP32, is stashed, and two drainer warps scale it by
+// 2^-(eA+eB) (exact) and add it into a double-float (2 x FP32) accumulator in global memory while
+// the next chunk's MMAs run; GB300's FP64 rate (~1.2 TFLOP/s) would make an FP64 read-modify-write
+// here the bottleneck.
 //
 // Both operands' digits are formed once per call by the row preparation, as the exact
 // shared-memory image of each K-block: the Re rows (a, b) of every row (the row image), and the
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     // while the next chunk runs. Every chunk end is announced (pieces as an empty stash), so a
     // drainer never waits longer than one chunk. A warp whose wait on the drainers times out
     // ("ddead") stops stashing and waiting; the error flag is set.
-    float2* const fscr = p.fscr + (size_t)blockIdx.x * kFscrPerCta;
+    float* const fscr = reinterpret_cast<float*>(p.fscr + (size_t)blockIdx.x * kFscrPerCta);
     int ns = 0;  // chunk ends announced
     bool ddead = false;
     // A warp whose wait timed out ("dead", warp-uniform) skips waits and work for the rest of its
@@ -780,11 +781,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
               tmem_ld_x8(tl + TMEM_L12 + col0, *reinterpret_cast<uint32_t(*)[8]>(&r1[0]));
             }
             tmem_ld_wait();
-            // stash both levels as they are (whole tile or piece); the drainers scale and add them
+            // stash the two levels' sum rounded once to FP32 (whole tile or piece); the drainers scale
+            // and add it. Its rounding, 2^-24 of the chunk's value and unbiased, sits far below the
+            // truncation error the level-1+2 accumulator already carries, and halves the stash.
             if (ddead) continue;
 #pragma unroll
             for (int jj = 0; jj < 16; ++jj)
-              if (jj < cnt) fscr[(col0 + jj) * 128 + m_row] = make_float2(__uint_as_float(r0[jj]), __uint_as_float(r1[jj]));
+              if (jj < cnt) fscr[(col0 + jj) * 128 + m_row] = __fadd_rn(__uint_as_float(r0[jj]), __uint_as_float(r1[jj]));
           }
           tc_fence_before();
           __threadfence_block();  // the stash is visible before it is announced
@@ -824,7 +827,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
     // writes; pieces of split tiles go into the piece's own partial buffer ([n][m], as the stash),
     // written rather than added on the piece's first chunk.
     const int mlo = (warp - 2 - NBG / 32) * 32 + lane;
-    const float2* const fscr = p.fscr + (size_t)blockIdx.x * kFscrPerCta;
+    const float* const fscr = reinterpret_cast<const float*>(p.fscr + (size_t)blockIdx.x * kFscrPerCta);
     for (int nd = 0;; ++nd) {
       if (!mbar_wait_bounded(stashed, nd & 1, kWaitNs)) {
         if (lane == 0) atomicCAS(p.d_err, DEV_OK, DEV_TIMEOUT);
@@ -846,7 +849,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
         if (!whole || I < bd.n_pb) {
           const float scA = exp2i(-bd.expA[(size_t)c * bd.n_pad + I]);  // the Re and Im rows of I share it
           for (int n0 = 0; n0 < N; n0 += 8) {
-            float2 x[16], v[16];
+            float x[16];
+            float2 v[16];
             float sc[8];
             size_t off[8];
             uint32_t okm = 0;
@@ -866,10 +870,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
 #pragma unroll
             for (int e = 0; e < 8; ++e)
               if (okm & (1u << e)) {
-                df_add(v[2 * e], x[2 * e].x * sc[e]);
-                df_add(v[2 * e], x[2 * e].y * sc[e]);
-                df_add(v[2 * e + 1], x[2 * e + 1].x * sc[e]);
-                df_add(v[2 * e + 1], x[2 * e + 1].y * sc[e]);
+                df_add(v[2 * e], x[2 * e] * sc[e]);
+                df_add(v[2 * e + 1], x[2 * e + 1] * sc[e]);
                 dst[off[e]] = v[2 * e];
                 dst[off[e] + hs] = v[2 * e + 1];
               }
