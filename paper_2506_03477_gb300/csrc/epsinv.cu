@@ -78,21 +78,26 @@ __device__ __forceinline__ double i128_to_double(long long hi, long long lo, int
 // written whole to sbuf[l], column-major SB x SB, zeros above the diagonal). The panel kernel forms
 // S = X^H X from it. info[l] keeps the first non-positive pivot (1-based global index); a failed
 // pivot continues with 1 so the sweep runs to its end, and that frequency's result is unspecified.
+// X is formed alongside the factorisation by forward elimination on [L | I]: once column j of L is
+// final, row j of X is scaled by 1/L_jj and subtracted, times L_ij, from every row i > j. Each step
+// is a rank-1 update over all threads, like the factorisation's own; FP64 issue is scarce on this
+// GPU, so no thread runs a long serial chain.
 __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ w, int n, int k0, int bk,
                                                           double2* __restrict__ sbuf, int* __restrict__ info) {
   const int l = blockIdx.x, t = threadIdx.x;
   double2* m = w + (size_t)l * n * n;
-  __shared__ double2 a[SB][SB + 1];  // a[i][j] = A(k0 + i, k0 + j), lower triangle
-  __shared__ double2 x[SB][SB + 1];  // x = L^{-1}, lower triangle
-  __shared__ double rdiag[SB];       // 1 / L_ii
+  __shared__ double2 a[SB][SB + 1];  // a[i][j] = A(k0 + i, k0 + j), lower triangle; becomes L
+  __shared__ double2 x[SB][SB + 1];  // becomes X = L^{-1}; starts as the identity
+  __shared__ double rdiag;           // 1 / L_jj of the current step
   __shared__ int fail;
   if (t == 0) fail = 0;
-  for (int e = t; e < bk * bk; e += blockDim.x) {
-    const int i = e % bk, j = e / bk;
-    if (i >= j) a[i][j] = m[(size_t)(k0 + j) * n + k0 + i];
+  for (int e = t; e < SB * SB; e += blockDim.x) {
+    const int i = e % SB, j = e / SB;
+    if (i < bk && j < bk && i >= j) a[i][j] = m[(size_t)(k0 + j) * n + k0 + i];
+    x[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
-  for (int j = 0; j < bk; ++j) {  // right-looking Cholesky of the block
+  for (int j = 0; j < bk; ++j) {
     if (t == 0) {  // one thread: an FP64 square root and division cost dozens of FP64 operations
       double d = a[j][j].x;
       if (!(d > 0.0)) {
@@ -101,17 +106,21 @@ __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ 
       }
       const double r = sqrt(d);
       a[j][j] = make_double2(r, 0.0);
-      rdiag[j] = 1.0 / r;
+      rdiag = 1.0 / r;
     }
     __syncthreads();
-    const double ri = rdiag[j];
-    for (int i = j + 1 + t; i < bk; i += blockDim.x) {
+    const double ri = rdiag;
+    for (int i = j + 1 + t; i < bk; i += blockDim.x) {  // column j of L
       a[i][j].x *= ri;
       a[i][j].y *= ri;
     }
+    for (int k = t; k <= j; k += blockDim.x) {  // row j of X is final
+      x[j][k].x *= ri;
+      x[j][k].y *= ri;
+    }
     __syncthreads();
     const int mt = bk - j - 1;
-    for (int e = t; e < mt * mt; e += blockDim.x) {
+    for (int e = t; e < mt * mt; e += blockDim.x) {  // trailing update of A
       const int i = j + 1 + e % mt, c = j + 1 + e / mt;
       if (i >= c) {
         const double2 p = cmul(a[i][j], conj2(a[c][j]));
@@ -119,27 +128,18 @@ __global__ void __launch_bounds__(256) sweep_pivot_kernel(double2* __restrict__ 
         a[i][c].y -= p.y;
       }
     }
+    for (int e = t; e < mt * (j + 1); e += blockDim.x) {  // X rows below j: x_ik -= L_ij x_jk
+      const int i = j + 1 + e % mt, k = e / mt;
+      const double2 p = cmul(a[i][j], x[j][k]);
+      x[i][k].x -= p.x;
+      x[i][k].y -= p.y;
+    }
     __syncthreads();
   }
-  if (t < bk) {  // column t of L^{-1} by forward substitution
-    const int j = t;
-    for (int i = 0; i < j; ++i) x[i][j] = make_double2(0.0, 0.0);
-    x[j][j] = make_double2(rdiag[j], 0.0);
-    for (int i = j + 1; i < bk; ++i) {
-      double sr = 0.0, si = 0.0;
-      for (int c = j; c < i; ++c) {
-        const double2 u = a[i][c], v = x[c][j];
-        sr = fma(u.x, v.x, fma(-u.y, v.y, sr));
-        si = fma(u.x, v.y, fma(u.y, v.x, si));
-      }
-      x[i][j] = make_double2(-sr * rdiag[i], -si * rdiag[i]);
-    }
-  }
-  __syncthreads();
   double2* xs = sbuf + (size_t)l * SB * SB;
   for (int e = t; e < SB * SB; e += blockDim.x) {
     const int i = e % SB, j = e / SB;
-    xs[j * SB + i] = (i < bk && j < bk) ? x[i][j] : make_double2(0.0, 0.0);
+    xs[j * SB + i] = (i < bk && j < bk && i >= j) ? x[i][j] : make_double2(0.0, 0.0);
   }
   if (t == 0 && fail != 0 && info[l] == 0) info[l] = k0 + fail;
 }

@@ -271,12 +271,20 @@ __global__ void __launch_bounds__(256) prep_max_kernel(const __grid_constant__ P
   const int I = it * TI + il;
   const bool rowok = I < B.n_pb;
   float m = 0.f;
-  for (int jc = q; jc < CHR; jc += 4) {
-    const long long r = (long long)c * CHR + jc;
-    if (rowok && r < K) {
-      const TZ z = Z[I + r * ldz];
-      const float s = row_weight(B.wst, r, p.L);
-      m = fmaxf(m, s * fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
+  constexpr int U = 8;  // loads in flight per thread
+  for (int jc0 = q; jc0 < CHR; jc0 += 4 * U) {
+    TZ z[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long r = (long long)c * CHR + jc0 + 4 * u;
+      z[u] = TZ{};
+      if (rowok && r < K) z[u] = Z[I + r * ldz];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long r = (long long)c * CHR + jc0 + 4 * u;
+      const float s = row_weight(B.wst, r, p.L);  // columns past K: z = 0
+      m = fmaxf(m, s * fmaxf(fabsf((float)z[u].x), fabsf((float)z[u].y)));
     }
   }
   red[q][il] = m;
