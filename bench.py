@@ -816,11 +816,20 @@ def main():
     print(json.dumps(out))
 
 
+def default_tile_width(n_pb, n_omega):
+    """The library's default J columns per tile for one block: among the widths t with t * L a multiple
+    of 16 and at most 256, from the widest down to 3/4 of it, the one whose J tiles overhang n_pb
+    least (the wider on a tie)."""
+    ok = [t for t in range(256 // n_omega, 0, -1) if (t * n_omega) % 16 == 0]
+    t0 = ok[0]
+    return min((t for t in ok if 4 * t >= 3 * t0), key=lambda t: (-(-n_pb // t) * t, -t))
+
+
 def issued_mma_flops(n_pb, n_omega, k_cols, TJ=None):
-    """BF16 MMA flops one accumulate call over k_cols columns issues (same tiling rules as the library;
-    TJ = the tile plan's columns per tile, default the widest)."""
+    """FP16 MMA flops one accumulate call over k_cols columns issues (same tiling rules as the library;
+    TJ = the tile plan's columns per tile, default the library's default width)."""
     if not TJ:
-        TJ = next(t for t in range(min(256 // n_omega, 32), 0, -1) if (t * n_omega) % 16 == 0)
+        TJ = default_tile_width(n_pb, n_omega)
     n = TJ * n_omega
     n_pad = (n_pb + 63) // 64 * 64
     n_it, n_jt = n_pad // 64, (n_pb + TJ - 1) // TJ

@@ -935,6 +935,24 @@ static int tile_width(int L) {
 
 int mixed_tile_cols(int L) { return L >= 1 && L <= kMaxOmega ? tile_width(L) : 0; }
 
+// Default width for one block of n_pb rows: among the valid widths down to 3/4 of the widest, the one
+// whose J tiles overhang n_pb least (the overhang is padding the MMAs compute), the wider on a tie.
+// n_pb = 428 at L = 1: 224 (2 J tiles, 448 rows) rather than 256 (512 rows).
+static int tile_width_for(int L, int n_pb) {
+  const int t0 = tile_width(L);
+  int best = t0;
+  long long best_rows = (long long)(n_pb + t0 - 1) / t0 * t0;
+  for (int t = t0 - 1; 4 * t >= 3 * t0; --t) {
+    if (!tile_width_ok(t, L)) continue;
+    const long long rows = (long long)(n_pb + t - 1) / t * t;
+    if (rows < best_rows) {
+      best = t;
+      best_rows = rows;
+    }
+  }
+  return best;
+}
+
 bool mixed_plan_valid(int L, const TilePlan& p) {
   return L >= 1 && L <= kMaxOmega && (p.tj == 0 || tile_width_ok(p.tj, L)) && p.pieces >= 0 && p.pieces <= 64;
 }
@@ -1186,7 +1204,8 @@ qsgw_status mixed_accumulate_batch(MixedScratch& s, int nb, const MixedBlock* in
         if (e.L == L && e.ca == ca && e.cc == cc) plan = e.plan;
     }
   }
-  const int TJ = plan.tj > 0 ? plan.tj : tile_width(L), N = TJ * L;
+  const int TJ = plan.tj > 0 ? plan.tj : (nb == 1 && !restricted ? tile_width_for(L, in[0].n_pb) : tile_width(L));
+  const int N = TJ * L;
   if (!tile_width_ok(TJ, L)) return QSGW_ERR_ARG;
   if (s.n_sm == 0) {
     int dev = 0;
