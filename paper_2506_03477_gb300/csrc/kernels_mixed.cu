@@ -656,12 +656,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) herk_mixed_kernel(MainArgs p) {
             const uint64_t b1 = make_smem_desc(bo + BPLANE, 128, 512, 0);
             const uint64_t b2 = make_smem_desc(bo + 2 * BPLANE, 128, 512, 0);
             const uint32_t acc_in = (kbl == 0 && ks == 0) ? 0u : 1u;
-            mma_f16(tmem, a0, b0, idesc, acc_in);
-            mma_f16(tmem + TMEM_L12, a0, b1, idesc, acc_in);
-            mma_f16(tmem + TMEM_L12, a1, b0, idesc, 1u);
-            mma_f16(tmem + TMEM_L12, a0, b2, idesc, 1u);
+            // grouped by A digit, so each A plane is read from shared memory once per K-step and
+            // kept in the collector buffer for the products that follow
+            mma_f16_a_fill(tmem, a0, b0, idesc, acc_in);
+            mma_f16_a_use(tmem + TMEM_L12, a0, b1, idesc, acc_in);
+            mma_f16_a_lastuse(tmem + TMEM_L12, a0, b2, idesc, 1u);
+            mma_f16_a_fill(tmem + TMEM_L12, a1, b0, idesc, 1u);
+            mma_f16_a_lastuse(tmem + TMEM_L12, a1, b1, idesc, 1u);
             mma_f16(tmem + TMEM_L12, a2, b0, idesc, 1u);
-            mma_f16(tmem + TMEM_L12, a1, b1, idesc, 1u);
           }
           mma_commit(&empty[s]);
           if (kbl == KB_PER_CH - 1 || kbi == nkb - 1) mma_commit(accfull);  // an item ends a chunk
