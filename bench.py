@@ -46,8 +46,8 @@ CONFIG_NAME = "medium chi0+W: n_pb=1500, n_k=64, n_occ=40, n_unocc=400 (K=1,024,
 # DRAM traffic of one herk_mixed_kernel launch of this workload (one k-point), from the ncu
 # capture summarised in profiles/herk_mixed_kernel_medium_one_kpoint.md; valid only for the kernel
 # source it was measured on (sha1 prefix), otherwise reported as null.
-TRAFFIC_BYTES_PER_LAUNCH = 25.937e9
-TRAFFIC_KERNEL_SHA1 = "e0f3fd21f7f8"
+TRAFFIC_BYTES_PER_LAUNCH = 13.866e9
+TRAFFIC_KERNEL_SHA1 = "aa25a5064d66"
 
 
 def measured_traffic():
