@@ -349,7 +349,7 @@ qsgw_status qsgw_selftest_wait_timeout(double limit_seconds, void *cuda_stream);
  * API instead). The columns go through the array one chunk of 1024 at a time, so their number
  * does not count: n_pb <= 256 always fits, with any n_occ * n_unocc. The space left after the
  * accumulators and one chunk's digit planes holds one flush area per CTA, and the tensor-core grid
- * is capped at the CTAs it has room for (about 80 at n_pb = 256 with 16 frequencies, the SM count for
+ * is capped at the CTAs it has room for (about 90 at n_pb = 256 with 16 frequencies, the SM count for
  * smaller blocks). Every call looks
  * up the array's device address in the current context (and sets the kernel's shared-memory
  * limit there), so the call stays valid after the context is reset. All calls share the one
