@@ -243,7 +243,7 @@ def run_ours(args, rank, world, dev_index):
 
         e2e_step()
         # the box's own pinned host-to-device rate on one k-point slab (context for the e2e figure:
-        # the 24.6 GB per step cross the host link once, overlapped with the kernels)
+        # Z crosses the host link once per step, overlapped with the kernels)
         probe = torch.empty(Zh[0].shape, dtype=Zh.dtype, device=dev)
         pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -252,7 +252,7 @@ def run_ours(args, rank, world, dev_index):
                 probe.copy_(Zh[0], non_blocking=True)
             pb.record(stream)
         stream.synchronize()
-        h2d_gbs = 4 * Zh[0].numel() * 16 / (pa.elapsed_time(pb) * 1e-3) / 1e9
+        h2d_gbs = 4 * Zh[0].numel() * Zh.element_size() / (pa.elapsed_time(pb) * 1e-3) / 1e9
         del probe
         barrier(world)
         t = time.perf_counter()
