@@ -387,15 +387,27 @@ __global__ void __launch_bounds__(256) sweep_digits_kernel(int n, int bk, const 
   }
 }
 
-// Grid (lower 64 x 64 tiles, frequency), 512 threads, one CTA per SM (168 KB of operand images, 448
-// TMEM columns). One thread moves the two images with bulk copies and issues the 112 MMAs; the 16
-// warps then read TMEM (warp w: lane quarter w mod 4, i.e. lane m = row m mod 64 of the tile, Re part
-// for m < 64 and Im part above; columns 16 (w / 4) .. + 16), combine the 7 levels and update their
-// half of each element: the same element rules as sweep_update_kernel. Every wait is bounded (1 s);
-// a wait that gives up sets DEV_TIMEOUT, issues no MMA and leaves the tile unchanged.
-constexpr int TC_THREADS = 512;
+// Persistent: one CTA per SM runs the (frequency, lower 64 x 64 tile) items item = blockIdx.x +
+// k gridDim.x, one CTA per SM (168 KB of operand images, 448 TMEM columns). Warp 16, one thread:
+// bulk copies of an item's two images, its 112 MMAs, and, as soon as those MMAs are done (the
+// images are free), the copies of the next item, so they overlap this item's epilogue. Warps 0..15
+// (epilogue): read TMEM (warp w: lane quarter w mod 4, i.e. lane m = row m mod 64 of the tile, Re
+// part for m < 64 and Im part above; columns 16 (w / 4) .. + 16), combine the 7 levels and update
+// their half of each element (the element rules of sweep_update_kernel), then free TMEM for the
+// next item's MMAs. Every wait is bounded (1 s); one that gives up sets DEV_TIMEOUT and the CTA
+// stops at the next item (tiles not reached are left unchanged).
+constexpr int TC_EPI = 512;               // epilogue threads
+constexpr int TC_THREADS = TC_EPI + 32;   // + the copy / MMA warp
+__device__ __forceinline__ void tc_item(int item, int tiles, int& l, int& ti, int& tj) {
+  l = item / tiles;
+  const int tile = item - l * tiles;
+  ti = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);  // lower tile (ti, tj), ti >= tj
+  while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+  while (ti * (ti + 1) / 2 > tile) --ti;
+  tj = tile - ti * (ti + 1) / 2;
+}
 __global__ void __launch_bounds__(TC_THREADS, 1) sweep_update_tc_kernel(double2* __restrict__ w, int n, int k0, int bk,
-                                                                        const double2* __restrict__ pbuf,
+                                                                        int L, const double2* __restrict__ pbuf,
                                                                         const uint8_t* __restrict__ imgA,
                                                                         const uint8_t* __restrict__ imgB,
                                                                         const int* __restrict__ eP,
@@ -404,24 +416,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_update_tc_kernel(double2*
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = sA + IMG_A;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + IMG_B);  // [0] operands landed, [1] MMAs done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
-  int* sok = reinterpret_cast<int*>(tmem_slot + 1);
-  int* sE = sok + 1;  // [64] grid exponents of the tile's rows (P), [64] of its columns (C)
-  const int l = blockIdx.y, t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  int ti = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);  // lower tile (ti, tj), ti >= tj
-  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
-  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
-  const int tj = blockIdx.x - ti * (ti + 1) / 2;
+  // [0] images landed, [1] MMAs done (images free, accumulators ready), [2] TMEM read out (16 warps)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + IMG_B);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
+  int* sabort = reinterpret_cast<int*>(tmem_slot + 1);  // set by the copy / MMA thread when it gives up
+  int* sdec = sabort + 1;  // [2] the epilogue warps' common stop decision, by item parity
+  int* sE = sdec + 2;      // [64] grid exponents of the item's rows (P), [64] of its columns (C)
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int ntr = (n + ST - 1) / ST;
+  const int tiles = ntr * (ntr + 1) / 2, items = tiles * L;
   if (t == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
-    *sok = 1;
+    mbar_init(&bars[2], TC_EPI / 32);
+    *sabort = 0;
+    sdec[0] = sdec[1] = 0;
     fence_mbar_init();
   }
-  if (t < 2 * ST)
-    sE[t] = t < ST ? eP[(size_t)l * ntr * ST + ti * ST + t] : eC[(size_t)l * ntr * ST + tj * ST + t - ST];
   if (warp == 0) {
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
@@ -430,88 +441,134 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_update_tc_kernel(double2*
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  if (t == 0) {
-    mbar_arrive_expect_tx(&bars[0], IMG_A + IMG_B);
-    bulk_g2s(sA, imgA + ((size_t)l * ntr + ti) * IMG_A, IMG_A, &bars[0]);
-    bulk_g2s(sB, imgB + ((size_t)l * ntr + tj) * IMG_B, IMG_B, &bars[0]);
-    bool ok = mbar_wait_bounded(&bars[0], 0, kTcWaitNs);
-    if (ok) {
-      tc_fence_after();
+  if (warp == TC_EPI / 32) {
+    // ---------------- copies and MMAs (one thread)
+    if (lane == 0) {
+      auto load = [&](int item) {
+        int l, ti, tj;
+        tc_item(item, tiles, l, ti, tj);
+        mbar_arrive_expect_tx(&bars[0], IMG_A + IMG_B);
+        bulk_g2s(sA, imgA + ((size_t)l * ntr + ti) * IMG_A, IMG_A, &bars[0]);
+        bulk_g2s(sB, imgB + ((size_t)l * ntr + tj) * IMG_B, IMG_B, &bars[0]);
+      };
       const uint32_t idesc = make_idesc_f16_f32(128, ST);
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-      for (int lev = 0; lev < DL; ++lev) {
-        uint32_t acc = 0;
-        for (int i = 0; i <= lev; ++i) {
-          const int j = lev - i;
+      int k = 0;
+      bool inflight = false;  // copies issued and not yet waited for
+      if ((int)blockIdx.x < items) {
+        load(blockIdx.x);
+        inflight = true;
+      }
+      for (int item = blockIdx.x; item < items; item += gridDim.x, ++k) {
+        bool ok = mbar_wait_bounded(&bars[0], k & 1, kTcWaitNs);
+        inflight = !ok;
+        if (ok && k > 0) ok = mbar_wait_bounded(&bars[2], (k - 1) & 1, kTcWaitNs);  // TMEM read out
+        if (!ok) {
+          atomicCAS(d_err, DEV_OK, DEV_TIMEOUT);
+          *sabort = 1;
+          mbar_arrive(&bars[1]);  // (release: after the flag) lets the epilogue warps see it and leave
+          break;
+        }
+        tc_fence_after();
+        for (int lev = 0; lev < DL; ++lev) {
+          uint32_t acc = 0;
+          for (int i = 0; i <= lev; ++i) {
+            const int j = lev - i;
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint64_t ad = make_smem_desc(a0 + i * DIG_A + ks * 4096, 2048, 128, 0);
-            const uint64_t bd = make_smem_desc(b0 + j * DIG_B + ks * 2048, 16 * ST, 128, 0);
-            mma_f16(tmem + lev * ST, ad, bd, idesc, acc);
-            acc = 1;
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t ad = make_smem_desc(a0 + i * DIG_A + ks * 4096, 2048, 128, 0);
+              const uint64_t bd = make_smem_desc(b0 + j * DIG_B + ks * 2048, 16 * ST, 128, 0);
+              mma_f16(tmem + lev * ST, ad, bd, idesc, acc);
+              acc = 1;
+            }
+          }
+        }
+        mma_commit(&bars[1]);
+        if (item + (int)gridDim.x < items) {  // the images are free once the MMAs are done
+          if (!mbar_wait_bounded(&bars[1], k & 1, kTcWaitNs)) {
+            atomicCAS(d_err, DEV_OK, DEV_TIMEOUT);
+            *sabort = 1;
+            break;
+          }
+          load(item + gridDim.x);
+          inflight = true;
+        }
+      }
+      if (inflight) mbar_wait_bounded(&bars[0], k & 1, kTcWaitNs);  // no copy left landing at exit
+    }
+  } else {
+    // ---------------- epilogue warps
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int lm = quarter * 32 + lane;  // TMEM lane: row of the tile, Re (< 64) or Im part
+    const int row = lm & (ST - 1), part = lm >> 6;
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
+    int k = 0;
+    for (int item = blockIdx.x; item < items; item += gridDim.x, ++k) {
+      int l, ti, tj;
+      tc_item(item, tiles, l, ti, tj);
+      if (t < 2 * ST)
+        sE[t] = t < ST ? eP[(size_t)l * ntr * ST + ti * ST + t] : eC[(size_t)l * ntr * ST + tj * ST + t - ST];
+      const bool done = mbar_wait_bounded(&bars[1], k & 1, kTcWaitNs);
+      if (!done && lane == 0) {
+        atomicCAS(d_err, DEV_OK, DEV_TIMEOUT);
+        sdec[k & 1] = 1;
+      }
+      if (t == 0 && *((volatile int*)sabort)) sdec[k & 1] = 1;
+      tc_fence_after();
+      named_bar_sync(1, TC_EPI);  // sE written; this item's decision final (every warp reads the same)
+      if (sdec[k & 1]) break;
+      if (t == 0) sdec[(k + 1) & 1] = 0;  // written again only after this item's closing barrier
+      double2* m = w + (size_t)l * n * n;
+      const double2* P = pbuf + (size_t)l * SB * n;
+      const int I = ti * ST + row;
+      const int e_i = sE[row];
+      constexpr int CW = 4;  // columns per TMEM read round
+      for (int c0 = cg * 16; c0 < cg * 16 + 16; c0 += CW) {
+        uint32_t r[DL][CW];
+#pragma unroll
+        for (int lev = 0; lev < DL; ++lev) tmem_ld_x4(tl + lev * ST + c0, r[lev]);
+        tmem_ld_wait();
+        double val[CW], old[CW];
+        bool upd[CW];
+#pragma unroll
+        for (int jj = 0; jj < CW; ++jj) {
+          const int J = tj * ST + c0 + jj;
+          const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
+          upd[jj] = I < n && J < n && I >= J && !inI && !inJ;
+          // the level sums are exact integers below 2^23: combine them exactly, hi = a0 2^16 + a1 2^8
+          // + a2 and lo = a3 2^24 + a4 2^16 + a5 2^8 + a6, value = (hi 2^32 + lo) 2^(-48 - eP - eC),
+          // rounded once to double in integer arithmetic (the FP64 pipe only does the subtraction)
+          long long a[DL];
+#pragma unroll
+          for (int lev = 0; lev < DL; ++lev) a[lev] = __float2int_rn(__uint_as_float(r[lev][jj]));
+          const long long hi = a[0] * 65536LL + a[1] * 256LL + a[2];
+          const long long lo = a[3] * 16777216LL + a[4] * 65536LL + a[5] * 256LL + a[6];
+          const int ee = e_i + sE[ST + c0 + jj];  // |ee| <= 800: the result stays a normal double
+          val[jj] = i128_to_double(hi, lo, -48 - ee);
+        }
+        if (c0 + CW >= cg * 16 + 16) {  // the last TMEM read of this item: free it for the next MMAs
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars[2]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < CW; ++jj)  // the loads first, all independent
+          old[jj] = upd[jj] ? reinterpret_cast<const double*>(m + (size_t)(tj * ST + c0 + jj) * n + I)[part] : 0.0;
+#pragma unroll
+        for (int jj = 0; jj < CW; ++jj)
+          if (upd[jj]) reinterpret_cast<double*>(m + (size_t)(tj * ST + c0 + jj) * n + I)[part] = old[jj] - val[jj];
+        if (part == 0) {  // the pivot block's column and row take P (the Re thread writes both parts)
+#pragma unroll
+          for (int jj = 0; jj < CW; ++jj) {
+            const int J = tj * ST + c0 + jj;
+            if (I >= n || J >= n || I < J) continue;
+            const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
+            if (inI == inJ) continue;
+            m[(size_t)J * n + I] = inJ ? P[(size_t)(J - k0) * n + I] : conj2(P[(size_t)(I - k0) * n + J]);
           }
         }
       }
-    } else {
-      atomicCAS(d_err, DEV_OK, DEV_TIMEOUT);
-      *sok = 0;
-      mbar_wait_bounded(&bars[0], 0, kTcWaitNs);  // give the copies in flight a last chance to land
-    }
-    mma_commit(&bars[1]);  // arrives once the MMAs (if any) are done
-  }
-  __syncwarp();
-  const bool done = mbar_wait_bounded(&bars[1], 0, kTcWaitNs);
-  if (!done && lane == 0) atomicCAS(d_err, DEV_OK, DEV_TIMEOUT);
-  tc_fence_after();
-  __syncthreads();  // *sok is final
-  if (*sok && __all_sync(0xffffffffu, done)) {
-    double2* m = w + (size_t)l * n * n;
-    const double2* P = pbuf + (size_t)l * SB * n;
-    const int quarter = warp & 3, cg = warp >> 2;
-    const int lm = quarter * 32 + lane;       // TMEM lane: row of the tile, Re (< 64) or Im part
-    const int row = lm & (ST - 1), part = lm >> 6;
-    const int I = ti * ST + row;
-    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-    const int e_i = sE[row];
-    for (int c0 = cg * 16; c0 < cg * 16 + 16; c0 += 8) {
-      uint32_t r[DL][8];
-#pragma unroll
-      for (int lev = 0; lev < DL; ++lev) tmem_ld_x8(tl + lev * ST + c0, r[lev]);
-      tmem_ld_wait();
-      double val[8], old[8];
-      bool upd[8];
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int J = tj * ST + c0 + jj;
-        const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
-        upd[jj] = I < n && J < n && I >= J && !inI && !inJ;
-        // the level sums are exact integers below 2^23: combine them exactly, hi = a0 2^16 + a1 2^8
-        // + a2 and lo = a3 2^24 + a4 2^16 + a5 2^8 + a6, value = (hi 2^32 + lo) 2^(-48 - eP - eC),
-        // rounded once to double in integer arithmetic (the FP64 pipe only does the subtraction)
-        long long a[DL];
-#pragma unroll
-        for (int lev = 0; lev < DL; ++lev) a[lev] = __float2int_rn(__uint_as_float(r[lev][jj]));
-        const long long hi = a[0] * 65536LL + a[1] * 256LL + a[2];
-        const long long lo = a[3] * 16777216LL + a[4] * 65536LL + a[5] * 256LL + a[6];
-        const int ee = e_i + sE[ST + c0 + jj];  // |ee| <= 800: the result stays a normal double
-        val[jj] = i128_to_double(hi, lo, -48 - ee);
-      }
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj)  // the loads first, all independent
-        old[jj] = upd[jj] ? reinterpret_cast<const double*>(m + (size_t)(tj * ST + c0 + jj) * n + I)[part] : 0.0;
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj)
-        if (upd[jj]) reinterpret_cast<double*>(m + (size_t)(tj * ST + c0 + jj) * n + I)[part] = old[jj] - val[jj];
-      if (part == 0) {  // the pivot block's column and row take P (the Re thread writes both parts)
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int J = tj * ST + c0 + jj;
-          if (I >= n || J >= n || I < J) continue;
-          const bool inI = (unsigned)(I - k0) < (unsigned)bk, inJ = (unsigned)(J - k0) < (unsigned)bk;
-          if (inI == inJ) continue;
-          m[(size_t)J * n + I] = inJ ? P[(size_t)(J - k0) * n + I] : conj2(P[(size_t)(I - k0) * n + J]);
-        }
-      }
+      named_bar_sync(1, TC_EPI);  // every warp is done with sE before the next item writes it
     }
   }
   tc_fence_before();
@@ -523,13 +580,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_update_tc_kernel(double2*
 }
 
 static size_t tc_update_smem() { return 1024 + IMG_A + IMG_B + 64 + 2 * ST * sizeof(int); }
+static_assert(3 * 8 + 4 + 4 + 2 * 4 <= 64, "barriers, TMEM slot and the stop flags fit their 64 bytes");
 
 void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, double2* cbuf, uint8_t* dig,
                         int* d_info, int* d_err, cudaStream_t s) {
   const int nt = (n + ST - 1) / ST;
   const int tiles = nt * (nt + 1) / 2;
-  if (dig)  // the attribute belongs to the current context: set it on every call
+  int n_sm = 1;
+  if (dig) {  // the attribute belongs to the current context: set it on every call
     cudaFuncSetAttribute(sweep_update_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_update_smem());
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+      n_sm = 1;
+  }
   uint8_t* imgA = dig;
   uint8_t* imgB = imgA + (size_t)L * nt * IMG_A;
   int* eP = reinterpret_cast<int*>(imgB + (size_t)L * nt * IMG_B);
@@ -541,8 +605,8 @@ void launch_eps_inverse(double2* w, int n, int L, double2* sbuf, double2* pbuf, 
     if (n <= bk) break;  // a single block: nothing outside it to update
     if (dig) {
       sweep_digits_kernel<<<dim3(nt, L, 2), 256, 0, s>>>(n, bk, pbuf, cbuf, imgA, imgB, eP, eC);
-      sweep_update_tc_kernel<<<dim3(tiles, L), TC_THREADS, tc_update_smem(), s>>>(w, n, k0, bk, pbuf, imgA, imgB,
-                                                                                  eP, eC, d_err);
+      sweep_update_tc_kernel<<<std::min(n_sm, tiles * L), TC_THREADS, tc_update_smem(), s>>>(w, n, k0, bk, L, pbuf,
+                                                                                             imgA, imgB, eP, eC, d_err);
     } else {
       sweep_update_kernel<<<dim3(tiles, L), 256, 0, s>>>(w, n, k0, bk, pbuf, cbuf);
     }
