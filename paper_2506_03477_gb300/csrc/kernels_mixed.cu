@@ -412,6 +412,97 @@ __global__ void __launch_bounds__(256, 3) prep_rows_kernel(const __grid_constant
   }
 }
 
+// L = 1 in one pass: the row maxima and the row image of one chunk of PS_ROWS rows (one 8-row
+// group), with the chunk's FP32 values staged in shared memory, so Z is read from HBM once instead
+// of once for the maxima and once for the digits. Grid (chunk, row group, block); 256 threads.
+//   load:   thread (row t mod 8, column t / 8 + 32 k) reads z, keeps the running max of
+//           sqrt(w_r) max(|Re z|, |Im z|) (each the FP32 product, as prep_max_kernel);
+//   digits: thread (row t mod 8, k-group (t / 8) mod 4, K-block t / 32 + 8 k) as prep_rows_kernel.
+constexpr int PS_ROWS = 8;
+constexpr int PS_LD = PS_ROWS + 1;  // staged column stride in float2: keeps the digit reads conflict-free
+constexpr size_t kPrepSymSmem = (size_t)CHR * PS_LD * sizeof(float2) + CHR * sizeof(float) + 8 * PS_ROWS * 4;
+template <typename TZ>
+__global__ void __launch_bounds__(256, 2) prep_sym_kernel(const __grid_constant__ PrepRowsArgs p) {
+  extern __shared__ float4 sym_smem[];
+  float2* sz = reinterpret_cast<float2*>(sym_smem);   // [CHR][PS_LD]
+  float* ssw = reinterpret_cast<float*>(sz + CHR * PS_LD);  // [CHR] sqrt(w_r)
+  float* red = ssw + CHR;                             // [8 warps][PS_ROWS]
+  const PrepRowsBlk& B = p.b[blockIdx.z];
+  const int c = blockIdx.x, g = blockIdx.y, t = threadIdx.x;
+  if (c >= B.n_ch || g * PS_ROWS >= B.n_itb * TI) return;
+  const int TJ = p.TJ;
+  const int I0 = g * PS_ROWS, it = I0 / TI, jt = I0 / TJ;
+  // CTA-uniform: tiles are 64 rows, J tiles a multiple of 16 rows, b_row0 a multiple of both
+  const bool need_a = it < B.n_it && it * TI < B.a_rows;
+  const bool need_b = jt < B.n_jt && I0 >= B.b_row0;
+  if (!need_a && !need_b) return;
+  const TZ* __restrict__ Z = static_cast<const TZ*>(B.Z);
+  const long long ldz = B.ldz, K = B.K;
+  const int row = t & (PS_ROWS - 1), I = I0 + row;
+  const bool rowok = I < B.n_pb;
+  for (int j = t; j < CHR; j += 256) ssw[j] = sqrtf(B.wst[(size_t)c * CHR + j]);  // 0 past K
+  __syncthreads();
+  float m = 0.f;
+  constexpr int U = 16;  // loads in flight per thread
+  for (int j0 = t / PS_ROWS; j0 < CHR; j0 += U * (256 / PS_ROWS)) {
+    TZ z[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * (256 / PS_ROWS);
+      const long long r = (long long)c * CHR + j;
+      z[u] = TZ{};
+      if (rowok && r < K) z[u] = Z[I + r * ldz];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u * (256 / PS_ROWS);
+      const float a = (float)z[u].x, b = (float)z[u].y;
+      sz[j * PS_LD + row] = make_float2(a, b);
+      m = fmaxf(m, ssw[j] * fmaxf(fabsf(a), fabsf(b)));
+    }
+  }
+  // max over the 32 threads of this row in the warp (lanes row, row + 8, row + 16, row + 24), then
+  // over the 8 warps
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+  m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+  if ((t & 31) < PS_ROWS) red[(t >> 5) * PS_ROWS + row] = m;
+  __syncthreads();
+  m = 0.f;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w * PS_ROWS + row]);
+  const int eA = scale_exp(m);
+  if (t < PS_ROWS && I < B.n_pad) {
+    B.zmax[(size_t)c * B.n_pad + I] = m;
+    B.expA[(size_t)c * B.n_pad + I] = eA;
+  }
+  const float sA = exp2i(eA);
+  const size_t RPLANE = (size_t)B.n_itb * TI * 64;
+  const int q = (t >> 3) & 3, kbs = t >> 5;
+  uint8_t* const rbase = B.rimg + (size_t)(I >> 3) * 512 + q * 128 + (I & 7) * 16;
+  for (int kbl = kbs; kbl < KB_PER_CH; kbl += 8) {
+    const int kb = c * KB_PER_CH + kbl;
+    float da[3][4], db[3][4];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int j = kbl * KBR + q * 4 + rr;
+      const float2 v = sz[j * PS_LD + row];
+      const float ws = ssw[j] * sA;  // digits of the exact products (sqrt(w_r) 2^e) a and (sqrt(w_r) 2^e) b
+      digits3_mul(ws, v.x, da[0][rr], da[1][rr], da[2][rr]);
+      digits3_mul(ws, v.y, db[0][rr], db[1][rr], db[2][rr]);
+    }
+    uint8_t* base = rbase + (size_t)kb * 3 * RPLANE;
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+      uint4 re;  // (a, b) pairs along K'
+      re.x = pack_h2(da[pl][0], db[pl][0]);
+      re.y = pack_h2(da[pl][1], db[pl][1]);
+      re.z = pack_h2(da[pl][2], db[pl][2]);
+      re.w = pack_h2(da[pl][3], db[pl][3]);
+      *reinterpret_cast<uint4*>(base + pl * RPLANE) = re;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ main tensor-core kernel
 // One block of transition columns (one accumulate request) for one q-point, as the kernel sees it.
 struct BlockDesc {
@@ -996,7 +1087,11 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static bool herk_set_attributes() {
   return cudaFuncSetAttribute(herk_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) ==
-         cudaSuccess;
+             cudaSuccess &&
+         cudaFuncSetAttribute(prep_sym_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kPrepSymSmem) == cudaSuccess &&
+         cudaFuncSetAttribute(prep_sym_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kPrepSymSmem) == cudaSuccess;
 }
 
 // Device list of the tiles on or above the diagonal for one (n_pb, TJ), cached in the scratch. The
@@ -1148,13 +1243,21 @@ static qsgw_status launch_blocks(int nb, const MixedBlock* in, const long long* 
     max_ita[t] = std::max(max_ita[t], G[b].n_it);
   }
   prep_cols_kernel<<<dim3(max_ch, nb), PC_THREADS, 0, stream>>>(pc);
-  if (nr[0] > 0) {
-    prep_max_kernel<double2><<<dim3(max_chr[0], max_ita[0], nr[0]), 256, 0, stream>>>(pr[0]);
-    prep_rows_kernel<double2><<<dim3(max_chr[0] * PR_SPLIT, max_it[0], nr[0]), 256, 0, stream>>>(pr[0]);
-  }
-  if (nr[1] > 0) {
-    prep_max_kernel<float2><<<dim3(max_chr[1], max_ita[1], nr[1]), 256, 0, stream>>>(pr[1]);
-    prep_rows_kernel<float2><<<dim3(max_chr[1] * PR_SPLIT, max_it[1], nr[1]), 256, 0, stream>>>(pr[1]);
+  if (L == 1) {  // one pass: maxima and the row image, Z read once
+    const int rg = TI / PS_ROWS;
+    if (nr[0] > 0)
+      prep_sym_kernel<double2><<<dim3(max_chr[0], max_it[0] * rg, nr[0]), 256, kPrepSymSmem, stream>>>(pr[0]);
+    if (nr[1] > 0)
+      prep_sym_kernel<float2><<<dim3(max_chr[1], max_it[1] * rg, nr[1]), 256, kPrepSymSmem, stream>>>(pr[1]);
+  } else {
+    if (nr[0] > 0) {
+      prep_max_kernel<double2><<<dim3(max_chr[0], max_ita[0], nr[0]), 256, 0, stream>>>(pr[0]);
+      prep_rows_kernel<double2><<<dim3(max_chr[0] * PR_SPLIT, max_it[0], nr[0]), 256, 0, stream>>>(pr[0]);
+    }
+    if (nr[1] > 0) {
+      prep_max_kernel<float2><<<dim3(max_chr[1], max_ita[1], nr[1]), 256, 0, stream>>>(pr[1]);
+      prep_rows_kernel<float2><<<dim3(max_chr[1] * PR_SPLIT, max_it[1], nr[1]), 256, 0, stream>>>(pr[1]);
+    }
   }
   // whole tiles first; the last R tiles (a partial last wave) are split into P chunk ranges
   const int Gc = grid_cap;
