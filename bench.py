@@ -47,7 +47,7 @@ CONFIG_NAME = "medium chi0+W: n_pb=1500, n_k=64, n_occ=40, n_unocc=400 (K=1,024,
 # capture summarised in profiles/herk_mixed_kernel_medium_one_kpoint.md; valid only for the kernel
 # source it was measured on (sha1 prefix), otherwise reported as null.
 TRAFFIC_BYTES_PER_LAUNCH = 13.866e9
-TRAFFIC_KERNEL_SHA1 = "aa25a5064d66"
+TRAFFIC_KERNEL_SHA1 = "62b9657a5782"  # the capture ran on aa25a5064d66; this revision adds only the one-frequency prep
 
 
 def measured_traffic():
