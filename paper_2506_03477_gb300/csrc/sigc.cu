@@ -83,29 +83,41 @@ __global__ void __launch_bounds__(256) transpose_cols_kernel(const double2* __re
 __device__ __forceinline__ void put(double2* d, double2 x) { *d = x; }
 __device__ __forceinline__ void put(float2* d, double2 x) { *d = make_float2((float)x.x, (float)x.y); }
 
-// One CTA per stacked column (i, mu); column-major, S2 = Y0 + n_pb rows.
+// Grid (256-row blocks of the S2 = Y0 + n_pb stacked rows, frequency i, groups of SD_MU columns
+// mu); column-major output, column (i, mu). Thread r writes row r of the group's columns: the
+// weight w_i of a D row is loaded once for them all, and the group's loads are independent.
+constexpr int SD_MU = 16;
 template <typename T>
 __global__ void __launch_bounds__(256) stack_d_kernel(const double2* __restrict__ Zt, int M, int n_pb,
                                                       const double* __restrict__ w, long long NT, long long row0,
                                                       const double2* __restrict__ Wc, int Y0, T* __restrict__ Z2) {
-  const int col = blockIdx.x, i = col / n_pb, mu = col % n_pb;
+  const int r = blockIdx.x * 256 + threadIdx.x, i = blockIdx.y, mu0 = blockIdx.z * SD_MU;
   const int S2 = Y0 + n_pb;
-  T* dst = Z2 + (size_t)col * S2;
-  const double2* zt = Zt + (size_t)mu * M;
-  const double* wi = w + i * NT + row0;
-  const double2* wc = Wc + ((size_t)i * n_pb + mu) * n_pb;  // column mu of W^c_i: elements (nu, mu)
-  for (int r = threadIdx.x; r < S2; r += 256) {
-    double2 v = make_double2(0.0, 0.0);
-    if (r < M) {
-      const double x = wi[r];
-      const double2 z = zt[r];
-      v = make_double2(x * z.x, x * z.y);
-    } else if (r >= Y0) {
-      const double2 q = wc[r - Y0];
-      v = make_double2(q.x, -q.y);
-    }
-    put(dst + r, v);
+  if (r >= S2) return;
+  const int nmu = min(SD_MU, n_pb - mu0);
+  double2 v[SD_MU];
+  if (r < M) {
+    const double x = w[i * NT + row0 + r];
+#pragma unroll
+    for (int u = 0; u < SD_MU; ++u)
+      if (u < nmu) {
+        const double2 z = Zt[(size_t)(mu0 + u) * M + r];
+        v[u] = make_double2(x * z.x, x * z.y);
+      }
+  } else if (r >= Y0) {
+#pragma unroll
+    for (int u = 0; u < SD_MU; ++u)
+      if (u < nmu) {  // column mu of W^c_i: element (nu, mu), nu = r - Y0
+        const double2 q = Wc[((size_t)i * n_pb + mu0 + u) * n_pb + (r - Y0)];
+        v[u] = make_double2(q.x, -q.y);
+      }
+  } else {
+#pragma unroll
+    for (int u = 0; u < SD_MU; ++u) v[u] = make_double2(0.0, 0.0);
   }
+#pragma unroll
+  for (int u = 0; u < SD_MU; ++u)
+    if (u < nmu) put(Z2 + ((size_t)i * n_pb + mu0 + u) * S2 + r, v[u]);
 }
 
 // Element (I, J) of an accumulator (loc = J * n_pad + I), one frequency: FP64 complex, or the
@@ -165,11 +177,11 @@ void launch_transpose_cols(const double2* Z, long long ldz, int n_pb, long long 
 
 void launch_sigc_stack_d(const double2* Zt, int M, int n_pb, const double* w, long long NT, long long row0, int L,
                          const double2* Wc, int Y0, void* Z2, bool z32, cudaStream_t s) {
-  const int cols = L * n_pb;
+  const dim3 grid((Y0 + n_pb + 255) / 256, L, (n_pb + SD_MU - 1) / SD_MU);
   if (z32)
-    stack_d_kernel<float2><<<cols, 256, 0, s>>>(Zt, M, n_pb, w, NT, row0, Wc, Y0, static_cast<float2*>(Z2));
+    stack_d_kernel<float2><<<grid, 256, 0, s>>>(Zt, M, n_pb, w, NT, row0, Wc, Y0, static_cast<float2*>(Z2));
   else
-    stack_d_kernel<double2><<<cols, 256, 0, s>>>(Zt, M, n_pb, w, NT, row0, Wc, Y0, static_cast<double2*>(Z2));
+    stack_d_kernel<double2><<<grid, 256, 0, s>>>(Zt, M, n_pb, w, NT, row0, Wc, Y0, static_cast<double2*>(Z2));
 }
 
 void launch_sigc_stack_i(const void* accD, AccKind kind, int n_padD, int Y0, const double2* Zt, int n_qp, int nb,
