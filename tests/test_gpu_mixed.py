@@ -45,7 +45,9 @@ def test_tiny_mixed(N):
 @pytest.mark.parametrize("n_pb,n_occ,n_unocc,L", [(1, 1, 1, 1), (100, 3, 7, 5), (130, 5, 13, 16), (65, 7, 80, 12),
                                                   (200, 9, 61, 9), (70, 2, 300, 3),
                                                   # K = 2048 (one whole chunk), K = 2064 (a chunk + one K-block)
-                                                  (96, 16, 128, 12), (96, 8, 258, 12)])
+                                                  (96, 16, 128, 12), (96, 8, 258, 12),
+                                                  # one frequency: the sqrt(w) row image serves both operands
+                                                  (300, 9, 130, 1), (257, 16, 128, 1), (33, 3, 700, 1)])
 def test_ragged_shapes_mixed(N, n_pb, n_occ, n_unocc, L):
     wl = Workload(f"ragged {n_pb}", n_q=1, n_k=2, n_occ=n_occ, n_omega=L, s_div=50.0, n_pb_fixed=n_pb,
                   n_unocc_fixed=n_unocc, seed=11)
